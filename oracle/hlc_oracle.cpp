@@ -274,7 +274,13 @@ void truncate_lr(Mat& U, Mat& V, double eps) {
 // ---------------------------------------------------------------------------
 // Dense blocked Cholesky (lower, column-major, in place).  Returns 0, or
 // -(j+1) when pivot j is not positive (the NaN failure of Sec. 3).
+// A pivot counts as non-positive when it is at rounding level: below
+// 64 u times the diagonal entry it was reduced from (u = 2^-53).  Sec. 3
+// traces the failure to diagonal entries "very close to zero"; with a nugget
+// tau^2 > 0 every pivot is at least tau^2, far above this level.
 // ---------------------------------------------------------------------------
+constexpr double kPivotTol = 64.0 * 1.1102230246251565e-16;
+
 long dense_cholesky(double* A, long n) {
   const long nb = 64;
   for (long k = 0; k < n; k += nb) {
@@ -282,8 +288,9 @@ long dense_cholesky(double* A, long n) {
     // factor the diagonal block
     for (long j = k; j < k + b; ++j) {
       double d = A[j + j * n];
+      const double d0 = d;
       for (long p = k; p < j; ++p) d -= A[j + p * n] * A[j + p * n];
-      if (!(d > 0.0)) return -(j + 1);
+      if (!(d > kPivotTol * d0)) return -(j + 1);
       d = std::sqrt(d);
       A[j + j * n] = d;
       for (long i = j + 1; i < k + b; ++i) {
@@ -1026,8 +1033,9 @@ void chol(HCtx& H, int m) {
     const long n = M.D.m;
     for (long j = 0; j < n; ++j) {
       double d = M.D(j, j);
+      const double d0 = d;
       for (long p = 0; p < j; ++p) d -= M.D(j, p) * M.D(j, p);
-      if (!(d > 0.0)) {
+      if (!(d > kPivotTol * d0)) {
         H.err = -(H.cl(M.r).lo + j + 1);
         return;
       }
