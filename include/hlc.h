@@ -1,0 +1,178 @@
+/*
+ * hlc.h -- C ABI of the GB300 H-matrix Gaussian log-likelihood library.
+ *
+ * One evaluation of the joint Gaussian log-likelihood of a zero-mean Matern
+ * random field observed at n scattered 2-D locations (arXiv:1709.08625):
+ *
+ *   L(theta) = -n/2 log(2 pi) - 1/2 log det C(theta) - 1/2 z^T C(theta)^-1 z   (eq. 1)
+ *
+ * computed with a hierarchical (H-) matrix approximation C~ of the covariance
+ * (Sec. 2.2), its H-Cholesky factor L~, log det C~ = 2 sum log L~_ii and the
+ * triangular solve L~ v = z (eq. 2), with the quadratic form refined against
+ * C~ in FP64.  The covariance is the Matern function of eq. (3),
+ *
+ *   C(h) = sigma2 / (2^(nu-1) Gamma(nu)) (h/ell)^nu K_nu(h/ell),
+ *
+ * plus the nugget tau^2 on the diagonal (Sec. 4.1, eq. 4).
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns an int status: HLC_OK (0) or a negative HLC_ERR_*
+ *     code; hlc_serve_poll may also return HLC_PENDING (1).  Functions never
+ *     abort the process; hlc_strerror(status) gives a one-line description.
+ *   - Outputs go through out-parameters.  Opaque handles are owned by the
+ *     caller and released with the matching *_free / hlc_destroy.
+ *   - Array arguments are borrowed for the duration of the call only.  A
+ *     pointer may point to host memory or to device memory of the context's
+ *     device (detected per call); results are written to the same kind of
+ *     memory the caller passed.
+ *   - Points and data vectors are in the caller's order; the tree
+ *     permutation stays internal.
+ *   - A non-positive pivot in the factorisation (the NaN failure described in
+ *     Sec. 3) is reported as HLC_ERR_NOT_SPD; no NaN is returned.
+ *   - All device work of a context runs on the context's stream; calls on one
+ *     context must not overlap from several host threads.
+ */
+#ifndef HLC_H
+#define HLC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define HLC_OK 0
+#define HLC_PENDING 1
+#define HLC_ERR_ARG (-1)       /* invalid argument (null pointer, n <= 0, bad theta ...) */
+#define HLC_ERR_OOM (-2)       /* device or host allocation failed */
+#define HLC_ERR_NOT_SPD (-3)   /* non-positive pivot in the H-Cholesky factorisation */
+#define HLC_ERR_TIMEOUT (-4)   /* a bounded device wait expired */
+#define HLC_ERR_CUDA (-5)      /* a CUDA runtime call failed */
+#define HLC_ERR_RANK (-6)      /* a low-rank block needed more than kmax columns */
+#define HLC_ERR_STATE (-7)     /* call out of order (e.g. factor before assemble) */
+#define HLC_ERR_UNSUPPORTED (-8)
+#define HLC_ERR_NUMERIC (-9)   /* numerical breakdown (NaN in a factor or a sum) */
+
+/* ---- precision modes ---------------------------------------------------- */
+#define HLC_FP64 0   /* every stage in FP64 */
+#define HLC_MIXED 1  /* FP32 low-rank panels and updates; FP64 leaf POTRF,
+                        log-det, recompression SVD and refinement */
+
+typedef struct hlc_ctx hlc_ctx;   /* device, stream, workspaces; owns device memory */
+typedef struct hlc_tree hlc_tree; /* cluster tree + block-cluster tree of one point set */
+typedef struct hlc_hmat hlc_hmat; /* an assembled C~ or a factor L~ (device resident) */
+
+/* theta = (ell, nu, sigma2) of eq. (3) and the nugget tau^2 of eq. (4). */
+typedef struct {
+  double sigma2; /* variance, > 0 */
+  double ell;    /* range, > 0 */
+  double nu;     /* smoothness, > 0 */
+  double nugget; /* tau^2 >= 0, added to the diagonal */
+} hlc_theta;
+
+typedef struct {
+  int leaf;           /* n_min: largest leaf cluster (Sec. 2.2), 1..128 */
+  double eta;         /* standard admissibility parameter (App. A), > 0 */
+  double eps;         /* block accuracy of C~ and of the H-arithmetic (Sec. 2.2) */
+  int precision;      /* HLC_FP64 or HLC_MIXED */
+  double refine_tol;  /* stop refinement when |z - C~ x| <= refine_tol |z| */
+  int refine_maxit;   /* at most this many refinement corrections */
+  int kmax;           /* rank capacity of a low-rank block, 1..64 */
+} hlc_params;
+
+typedef struct {
+  double loglik;       /* L~(theta), eq. (2) with the refined quadratic form */
+  double logdet;       /* 2 sum log L~_ii */
+  double quad;         /* z^T x, x refined against C~ */
+  double quad_factor;  /* v^T v with L~ v = z (eq. 2 as printed) */
+  int refine_iters;    /* refinement corrections applied */
+  double rel_residual; /* |z - C~ x| / |z| at exit */
+  size_t bytes_C;      /* storage of C~ (actual ranks) */
+  size_t bytes_L;      /* storage of L~ (actual ranks) */
+  int max_rank_C, max_rank_L;
+  double ms_assemble, ms_factor, ms_solve; /* device time per phase */
+} hlc_result;
+
+/* Defaults: leaf 64, eta 2, eps 1e-6, HLC_FP64, refine_tol 1e-12,
+ * refine_maxit 30, kmax 64. */
+void hlc_default_params(hlc_params* p);
+
+/* Description of a status code (static string, never NULL). */
+const char* hlc_strerror(int status);
+
+/* Create a context on CUDA device `device` (its own stream and workspaces).
+ * HLC_ERR_CUDA if the device is absent. */
+int hlc_create(hlc_ctx** out, int device);
+void hlc_destroy(hlc_ctx* ctx);
+
+/*
+ * Cluster tree and block-cluster tree of n points (Sec. 2.2, Def. 2.2, App. A).
+ * xy: n x 2 row-major FP64 (x0, y0, x1, y1, ...), host or device.
+ * The points are Morton-sorted over their bounding box and bisected
+ * geometrically (longest axis of the tight bounding box, at its midpoint)
+ * down to clusters of at most p->leaf points; block pairs of the lower
+ * triangle with min(diam) <= eta * dist are admissible (low-rank), other
+ * pairs with a leaf cluster are dense.  Runs on the device.
+ * The parameters are copied into the tree and used by every later call on it.
+ */
+int hlc_build_tree(hlc_ctx* ctx, const double* xy, int64_t n, const hlc_params* p,
+                   hlc_tree** out);
+void hlc_tree_free(hlc_tree* t);
+
+/* info[8] = {n, clusters, leaf clusters, dense leaves, low-rank leaves,
+ *            depth, plan ops, plan waves}. */
+int hlc_tree_info(const hlc_tree* t, int64_t* info);
+/* perm[i] = caller index of the point at tree position i (host array of n). */
+int hlc_tree_perm(const hlc_tree* t, int32_t* perm);
+/* Leaf blocks, 5 int64 each {row lo, row hi, col lo, col hi, type (0 dense,
+ * 1 low-rank)} in tree positions, depth-first order; host array. */
+int hlc_tree_leaf_blocks(const hlc_tree* t, int64_t* out);
+
+/*
+ * Assemble C~(theta) (Sec. 2.2): dense leaves exactly, admissible leaves by
+ * ACA with partial pivoting (App. B) recompressed by QR+SVD to block
+ * accuracy eps (Remark A.1).  The result is owned by the caller.
+ */
+int hlc_assemble(hlc_ctx* ctx, hlc_tree* t, const hlc_theta* th, hlc_hmat** C);
+
+/* H-Cholesky C~ = L~ L~^T (Table 1) with truncation at eps; C is kept. */
+int hlc_cholesky(hlc_ctx* ctx, const hlc_hmat* C, hlc_hmat** L);
+
+/* y = C~ x (C~ symmetric, Table 1 matvec); x, y: n values in caller order. */
+int hlc_matvec(hlc_ctx* ctx, const hlc_hmat* C, const double* x, double* y);
+
+/* Dense expansion of C~ (symmetric) or L~ (lower) into an n x n column-major
+ * host array in caller order; for small n only (n <= 16384). */
+int hlc_hmat_expand(hlc_ctx* ctx, const hlc_hmat* M, double* out);
+
+/* Ranks of the low-rank leaves in hlc_tree_leaf_blocks order (-1 for dense). */
+int hlc_hmat_ranks(hlc_ctx* ctx, const hlc_hmat* M, int32_t* out);
+
+void hlc_hmat_free(hlc_hmat* M);
+
+/*
+ * One likelihood evaluation on an existing tree: assemble C~(theta), factor,
+ * log det, forward solve (eq. 2), FP64 refinement of C~^-1 z, assemble L.
+ * z: n values in caller order (host or device).  Uses the tree's cached
+ * workspace; no device allocation after the first call on a tree.
+ */
+int hlc_loglik(hlc_ctx* ctx, hlc_tree* t, const hlc_theta* th, const double* z,
+               hlc_result* out);
+
+/* ---- serving: continuous batching of likelihood requests ------------------ */
+/* Start the request loop with a device-memory budget and a slot limit. */
+int hlc_serve_start(hlc_ctx* ctx, size_t hbm_budget_bytes, int max_slots);
+/* Queue one request (copies xy and z); returns its id in *req_id. */
+int hlc_serve_submit(hlc_ctx* ctx, const double* xy, const double* z, int64_t n,
+                     const hlc_theta* th, const hlc_params* p, uint64_t* req_id);
+/* HLC_PENDING until done; then the request's status with *out filled. */
+int hlc_serve_poll(hlc_ctx* ctx, uint64_t req_id, hlc_result* out);
+/* Drain and stop the loop. */
+int hlc_serve_stop(hlc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HLC_H */

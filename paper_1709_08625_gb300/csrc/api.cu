@@ -1,0 +1,735 @@
+// api.cu -- the C ABI (include/hlc.h): contexts, trees, H-matrices and the
+// likelihood evaluation, executing the planner's op programs on one stream.
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <stdexcept>
+#include <vector>
+
+#include "engine.h"
+#include "kernels.h"
+#include "matern.cuh"
+#include "serve.h"
+
+using namespace hlc;
+
+// ---------------------------------------------------------------------------
+// handles
+// ---------------------------------------------------------------------------
+struct hlc_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  double* d_part = nullptr;   // reduction partials
+  double* d_scalar = nullptr; // 8 scalars
+  int* d_status = nullptr;    // [0] code, [1] detail
+  double* d_scratch = nullptr;
+  cudaEvent_t ev[4];
+  hlc::Serve* serve = nullptr;
+};
+
+struct hlc_hmat {
+  hlc_tree* t = nullptr;
+  int which = 0;  // 0: C~, 1: L~
+  double* arena = nullptr;
+  int* ranks = nullptr;
+  bool valid = false;
+};
+
+struct hlc_tree {
+  hlc_ctx* ctx = nullptr;
+  hlc_params p{};
+  HTree T;
+  int32_t* d_perm = nullptr;
+  double* d_px = nullptr;
+  double* d_py = nullptr;
+  DenseAsm* d_dense = nullptr;
+  LrAsm* d_lr = nullptr;
+  int64_t* d_diag_off = nullptr;
+  int32_t* d_diag_dim = nullptr;
+  int64_t ndiag = 0;
+  double* d_knu = nullptr;  // 2 * KNU_NODES node table
+  std::vector<double> h_knu;
+  Plan chol, fwd, bwd, mv, recomp;
+  bool chol_ready = false, solve_ready = false;
+  double* d_tmp = nullptr;
+  int64_t tmp_cap = 0;
+  double* d_vec = nullptr;  // 5 n: W0 | X | Y | Z | XS
+  hlc_hmat* wsC = nullptr;
+  hlc_hmat* wsL = nullptr;
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return HLC_OK;
+  if (e == cudaErrorMemoryAllocation) return HLC_ERR_OOM;
+  return HLC_ERR_CUDA;
+}
+
+#define CK(x)                             \
+  do {                                    \
+    cudaError_t e_ = (x);                 \
+    if (e_ != cudaSuccess) {              \
+      return cuda_status(e_);             \
+    }                                     \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+int upload(T** d, const std::vector<T>& h) {
+  *d = nullptr;
+  if (h.empty()) return HLC_OK;
+  CK(cudaMalloc(d, h.size() * sizeof(T)));
+  CK(cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return HLC_OK;
+}
+
+int upload_plan(Plan& P) {
+  int st;
+  P.checked = true;
+  if ((st = upload(&P.d_gemm, P.gemm))) return st;
+  if ((st = upload(&P.d_trsm, P.trsm))) return st;
+  if ((st = upload(&P.d_potrf, P.potrf))) return st;
+  if ((st = upload(&P.d_trunc, P.trunc))) return st;
+  if ((st = upload(&P.d_terms, P.terms))) return st;
+  return HLC_OK;
+}
+
+void free_plan(Plan& P) {
+  cudaFree(P.d_gemm);
+  cudaFree(P.d_trsm);
+  cudaFree(P.d_potrf);
+  cudaFree(P.d_trunc);
+  cudaFree(P.d_terms);
+  P.d_gemm = nullptr;
+  P.d_trsm = nullptr;
+  P.d_potrf = nullptr;
+  P.d_trunc = nullptr;
+  P.d_terms = nullptr;
+}
+
+int ensure_tmp(hlc_tree* t, int64_t doubles) {
+  if (doubles <= t->tmp_cap) return HLC_OK;
+  cudaFree(t->d_tmp);
+  t->d_tmp = nullptr;
+  t->tmp_cap = 0;
+  CK(cudaMalloc(&t->d_tmp, std::max<int64_t>(doubles, 4) * sizeof(double)));
+  t->tmp_cap = doubles;
+  return HLC_OK;
+}
+
+void run_plan(hlc_tree* t, const Plan& P, const Bases& B, cudaStream_t st) {
+  const int md = (int)std::max<int64_t>(t->T.max_dense_dim, t->T.leaf);
+  for (const Launch& L : P.launches) {
+    const void* ops = nullptr;
+    switch (L.type) {
+      case OP_GEMM: ops = P.d_gemm + L.first; break;
+      case OP_TRSM: ops = P.d_trsm + L.first; break;
+      case OP_POTRF: ops = P.d_potrf + L.first; break;
+      default: ops = P.d_trunc + L.first; break;
+    }
+    launch_ops(L.type, ops, L.count, P.d_terms, B, md, st);
+  }
+}
+
+Bases make_bases(hlc_tree* t, double* mat_L, double* mat_C, int* ranks) {
+  Bases B;
+  B.buf[BUF_L] = mat_L;
+  B.buf[BUF_TMP] = t->d_tmp;
+  B.buf[BUF_VEC] = t->d_vec;
+  B.buf[BUF_C] = mat_C;
+  B.ranks = ranks;
+  B.status = t->ctx->d_status;
+  B.scratch = t->ctx->d_scratch;
+  return B;
+}
+
+// device status -> ABI status (also resets it)
+int take_status(hlc_ctx* c) {
+  int h[2] = {0, 0};
+  cudaError_t e = cudaMemcpyAsync(h, c->d_status, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  cudaMemsetAsync(c->d_status, 0, 2 * sizeof(int), c->stream);
+  switch (h[0]) {
+    case DEV_OK: return HLC_OK;
+    case DEV_NOT_SPD: return HLC_ERR_NOT_SPD;
+    case DEV_RANK: return HLC_ERR_RANK;
+    default: return HLC_ERR_NUMERIC;
+  }
+}
+
+bool valid_theta(const hlc_theta* th) {
+  return th && th->sigma2 > 0.0 && th->ell > 0.0 && th->nu > 0.0 && th->nugget >= 0.0 && th->nu < 20.0;
+}
+
+MaternDev matern_params(hlc_tree* t, const hlc_theta* th) {
+  MaternDev mp;
+  mp.sigma2 = th->sigma2;
+  mp.ell = th->ell;
+  mp.nu = th->nu;
+  mp.nugget = th->nugget;
+  mp.coef = th->sigma2 / (pow(2.0, th->nu - 1.0) * tgamma(th->nu));
+  mp.kind = th->nu == 0.5 ? 0 : th->nu == 1.5 ? 1 : th->nu == 2.5 ? 2 : 3;
+  mp.nnodes = KNU_NODES;
+  t->h_knu.resize(2 * KNU_NODES);
+  for (int j = 0; j < KNU_NODES; ++j) {
+    const double tj = j * KNU_STEP;
+    const double sh = sinh(0.5 * tj);
+    t->h_knu[j] = 2.0 * sh * sh;  // cosh t - 1 without cancellation
+    t->h_knu[KNU_NODES + j] = cosh(th->nu * tj);
+  }
+  mp.cm1 = t->d_knu;
+  mp.wnu = t->d_knu + KNU_NODES;
+  return mp;
+}
+
+int hmat_alloc(hlc_tree* t, int which, hlc_hmat** out) {
+  hlc_hmat* M = new (std::nothrow) hlc_hmat();
+  if (!M) return HLC_ERR_OOM;
+  M->t = t;
+  M->which = which;
+  cudaError_t e = cudaMalloc(&M->arena, std::max<int64_t>(t->T.arena_doubles, 4) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&M->ranks, std::max<int32_t>(t->T.nslots, 1) * sizeof(int));
+  if (e != cudaSuccess) {
+    cudaFree(M->arena);
+    cudaFree(M->ranks);
+    delete M;
+    return cuda_status(e);
+  }
+  *out = M;
+  return HLC_OK;
+}
+
+// Refuse to run a plan whose views leave their buffers.
+int check_plan(hlc_tree* t, const Plan& P) {
+  int64_t sz[NBUF];
+  sz[BUF_L] = t->T.arena_doubles;
+  sz[BUF_C] = t->T.arena_doubles;
+  sz[BUF_TMP] = P.tmp_doubles;
+  sz[BUF_VEC] = 5 * t->T.n;
+  const std::string err = validate_plan(P, sz);
+  if (!err.empty()) {
+    fprintf(stderr, "hlc: plan rejected: %s\n", err.c_str());
+    return HLC_ERR_STATE;
+  }
+  return HLC_OK;
+}
+
+int build_plans(hlc_tree* t, bool chol, bool solve) {
+  try {
+    if (chol && !t->chol_ready) {
+      plan_cholesky(t->T, t->chol);
+      int st = check_plan(t, t->chol);
+      if (st) return st;
+      st = upload_plan(t->chol);
+      if (st) return st;
+      t->chol_ready = true;
+    }
+    if (solve && !t->solve_ready) {
+      const int64_t n = t->T.n;
+      plan_solve(t->T, t->fwd, 0, 0, 1);
+      plan_solve(t->T, t->bwd, 1, 0, 1);
+      plan_matvec(t->T, t->mv, n, 2 * n, 1);
+      int st;
+      if ((st = check_plan(t, t->fwd)) || (st = check_plan(t, t->bwd)) || (st = check_plan(t, t->mv))) return st;
+      if ((st = upload_plan(t->fwd)) || (st = upload_plan(t->bwd)) || (st = upload_plan(t->mv))) return st;
+      t->solve_ready = true;
+    }
+  } catch (const std::bad_alloc&) {
+    return HLC_ERR_OOM;
+  } catch (const std::exception&) {
+    return HLC_ERR_CUDA;
+  }
+  int64_t need = std::max(t->recomp.tmp_doubles, t->chol.tmp_doubles);
+  need = std::max(need, std::max(t->fwd.tmp_doubles, std::max(t->bwd.tmp_doubles, t->mv.tmp_doubles)));
+  return ensure_tmp(t, need);
+}
+
+int do_assemble(hlc_tree* t, const hlc_theta* th, hlc_hmat* C) {
+  hlc_ctx* c = t->ctx;
+  MaternDev mp = matern_params(t, th);
+  CK(cudaMemcpyAsync(t->d_knu, t->h_knu.data(), t->h_knu.size() * sizeof(double), cudaMemcpyHostToDevice,
+                     c->stream));
+  launch_dense_asm(t->d_dense, (int64_t)t->T.dense_asm.size(), C->arena, t->d_px, t->d_py, mp, c->stream);
+  launch_aca(t->d_lr, (int64_t)t->T.lr_asm.size(), C->arena, t->d_px, t->d_py, mp, t->p.eps, C->ranks,
+             c->stream);
+  Bases B = make_bases(t, nullptr, C->arena, C->ranks);
+  run_plan(t, t->recomp, B, c->stream);
+  CK(cudaGetLastError());
+  C->valid = false;
+  const int st = take_status(c);
+  if (st == HLC_OK) C->valid = true;
+  return st;
+}
+
+int do_cholesky(hlc_tree* t, const hlc_hmat* C, hlc_hmat* L) {
+  hlc_ctx* c = t->ctx;
+  int st = build_plans(t, true, false);
+  if (st) return st;
+  CK(cudaMemcpyAsync(L->arena, C->arena, t->T.arena_doubles * sizeof(double), cudaMemcpyDeviceToDevice,
+                     c->stream));
+  if (t->T.nslots)
+    CK(cudaMemcpyAsync(L->ranks, C->ranks, t->T.nslots * sizeof(int), cudaMemcpyDeviceToDevice, c->stream));
+  Bases B = make_bases(t, L->arena, nullptr, L->ranks);
+  run_plan(t, t->chol, B, c->stream);
+  CK(cudaGetLastError());
+  L->valid = false;
+  st = take_status(c);
+  if (st == HLC_OK) L->valid = true;
+  return st;
+}
+
+double read_scalar(hlc_ctx* c, int idx) {
+  double v = 0.0;
+  cudaMemcpyAsync(&v, c->d_scalar + idx, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  cudaStreamSynchronize(c->stream);
+  return v;
+}
+
+void hmat_stats(hlc_tree* t, const hlc_hmat* M, size_t* bytes, int* maxr) {
+  std::vector<int> r(t->T.nslots);
+  if (!r.empty()) cudaMemcpy(r.data(), M->ranks, r.size() * sizeof(int), cudaMemcpyDeviceToHost);
+  size_t b = 0;
+  int mx = 0;
+  for (int32_t bl : t->T.leaves) {
+    const Block& B = t->T.blk[bl];
+    if (B.type == BT_DENSE) {
+      b += (size_t)B.m * B.n * 8;
+    } else {
+      const int k = r[B.slot];
+      b += (size_t)(B.m + B.n) * k * 8;
+      mx = std::max(mx, k);
+    }
+  }
+  *bytes = b;
+  *maxr = mx;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void hlc_default_params(hlc_params* p) {
+  if (!p) return;
+  p->leaf = 64;
+  p->eta = 2.0;
+  p->eps = 1e-6;
+  p->precision = HLC_FP64;
+  p->refine_tol = 1e-12;
+  p->refine_maxit = 30;
+  p->kmax = 64;
+}
+
+const char* hlc_strerror(int s) {
+  switch (s) {
+    case HLC_OK: return "ok";
+    case HLC_PENDING: return "request pending";
+    case HLC_ERR_ARG: return "invalid argument";
+    case HLC_ERR_OOM: return "out of memory";
+    case HLC_ERR_NOT_SPD: return "matrix not positive definite (non-positive pivot)";
+    case HLC_ERR_TIMEOUT: return "bounded device wait expired";
+    case HLC_ERR_CUDA: return "CUDA runtime error";
+    case HLC_ERR_RANK: return "low-rank block exceeded the rank capacity kmax";
+    case HLC_ERR_STATE: return "call out of order";
+    case HLC_ERR_UNSUPPORTED: return "unsupported";
+    case HLC_ERR_NUMERIC: return "numerical breakdown (NaN)";
+    default: return "unknown status";
+  }
+}
+
+int hlc_create(hlc_ctx** out, int device) {
+  if (!out) return HLC_ERR_ARG;
+  *out = nullptr;
+  int nd = 0;
+  if (cudaGetDeviceCount(&nd) != cudaSuccess || device < 0 || device >= nd) {
+    cudaGetLastError();
+    return HLC_ERR_CUDA;
+  }
+  CK(cudaSetDevice(device));
+  hlc_ctx* c = new (std::nothrow) hlc_ctx();
+  if (!c) return HLC_ERR_OOM;
+  c->device = device;
+  cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_part, 1 << 20);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_scalar, 64);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_status, 16);
+  if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, 16);
+  if (e == cudaSuccess)
+    e = cudaMalloc(&c->d_scratch, (size_t)max_trunc_ctas() * trunc_scratch_doubles() * sizeof(double));
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&c->ev[i]);
+  if (e == cudaSuccess && configure_kernels(128) != 0) e = cudaErrorInvalidValue;
+  if (e != cudaSuccess) {
+    hlc_destroy(c);
+    return cuda_status(e);
+  }
+  *out = c;
+  return HLC_OK;
+}
+
+void hlc_destroy(hlc_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->serve) hlc_serve_stop(c);
+  cudaFree(c->d_part);
+  cudaFree(c->d_scalar);
+  cudaFree(c->d_status);
+  cudaFree(c->d_scratch);
+  for (int i = 0; i < 4; ++i)
+    if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+int hlc_build_tree(hlc_ctx* c, const double* xy, int64_t n, const hlc_params* p, hlc_tree** out) {
+  if (!c || !xy || !out || n <= 0 || n > (int64_t)1 << 30) return HLC_ERR_ARG;
+  hlc_params q;
+  if (p)
+    q = *p;
+  else
+    hlc_default_params(&q);
+  if (q.leaf < 1 || q.leaf > 128 || !(q.eta > 0.0) || !(q.eps > 0.0) || q.kmax < 1 || q.kmax > 64 ||
+      (q.precision != HLC_FP64 && q.precision != HLC_MIXED) || q.refine_maxit < 0)
+    return HLC_ERR_ARG;
+  *out = nullptr;
+  CK(cudaSetDevice(c->device));
+  std::unique_ptr<hlc_tree> t(new (std::nothrow) hlc_tree());
+  if (!t) return HLC_ERR_OOM;
+  t->ctx = c;
+  t->p = q;
+  // points to the host for the structure, to the device for the kernels
+  std::vector<double> hxy((size_t)2 * n);
+  double* d_xy = nullptr;
+  if (is_device_ptr(xy)) {
+    CK(cudaMemcpy(hxy.data(), xy, 2 * n * sizeof(double), cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(hxy.data(), xy, 2 * n * sizeof(double));
+  }
+  std::vector<double> hx(n), hy(n);
+  for (int64_t i = 0; i < n; ++i) {
+    hx[i] = hxy[2 * i];
+    hy[i] = hxy[2 * i + 1];
+  }
+  try {
+    tree_from_points(t->T, hx.data(), hy.data(), n, q.leaf, q.eta);
+    t->T.eps = q.eps;
+    block_tree(t->T);
+    layout(t->T, q.kmax);
+    plan_recompress(t->T, t->recomp);
+  } catch (const std::bad_alloc&) {
+    return HLC_ERR_OOM;
+  }
+  int st;
+  if ((st = upload(&t->d_perm, t->T.perm))) return st;
+  CK(cudaMalloc(&d_xy, 2 * n * sizeof(double)));
+  CK(cudaMemcpy(d_xy, hxy.data(), 2 * n * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMalloc(&t->d_px, n * sizeof(double)));
+  CK(cudaMalloc(&t->d_py, n * sizeof(double)));
+  launch_points(d_xy, t->d_perm, t->d_px, t->d_py, n, c->stream);
+  CK(cudaStreamSynchronize(c->stream));
+  cudaFree(d_xy);
+  if ((st = upload(&t->d_dense, t->T.dense_asm))) return st;
+  if ((st = upload(&t->d_lr, t->T.lr_asm))) return st;
+  std::vector<int64_t> doff;
+  std::vector<int32_t> ddim;
+  for (int32_t b : t->T.leaves) {
+    const Block& B = t->T.blk[b];
+    if (B.diag) {
+      doff.push_back(B.offD);
+      ddim.push_back((int32_t)B.m);
+    }
+  }
+  t->ndiag = (int64_t)doff.size();
+  if ((st = upload(&t->d_diag_off, doff))) return st;
+  if ((st = upload(&t->d_diag_dim, ddim))) return st;
+  CK(cudaMalloc(&t->d_knu, 2 * KNU_NODES * sizeof(double)));
+  CK(cudaMalloc(&t->d_vec, 5 * n * sizeof(double)));
+  if ((st = check_plan(t.get(), t->recomp))) return st;
+  if ((st = upload_plan(t->recomp))) return st;
+  if ((st = ensure_tmp(t.get(), t->recomp.tmp_doubles))) return st;
+  *out = t.release();
+  return HLC_OK;
+}
+
+void hlc_tree_free(hlc_tree* t) {
+  if (!t) return;
+  cudaSetDevice(t->ctx->device);
+  cudaStreamSynchronize(t->ctx->stream);
+  hlc_hmat_free(t->wsC);
+  hlc_hmat_free(t->wsL);
+  cudaFree(t->d_perm);
+  cudaFree(t->d_px);
+  cudaFree(t->d_py);
+  cudaFree(t->d_dense);
+  cudaFree(t->d_lr);
+  cudaFree(t->d_diag_off);
+  cudaFree(t->d_diag_dim);
+  cudaFree(t->d_knu);
+  cudaFree(t->d_tmp);
+  cudaFree(t->d_vec);
+  free_plan(t->chol);
+  free_plan(t->fwd);
+  free_plan(t->bwd);
+  free_plan(t->mv);
+  free_plan(t->recomp);
+  delete t;
+}
+
+int hlc_tree_info(const hlc_tree* t, int64_t* info) {
+  if (!t || !info) return HLC_ERR_ARG;
+  int64_t leaves = 0, nd = 0, nl = 0;
+  for (const Cluster& c : t->T.cl) leaves += c.leaf() ? 1 : 0;
+  for (int32_t b : t->T.leaves) (t->T.blk[b].type == BT_DENSE ? nd : nl)++;
+  info[0] = t->T.n;
+  info[1] = (int64_t)t->T.cl.size();
+  info[2] = leaves;
+  info[3] = nd;
+  info[4] = nl;
+  info[5] = t->T.depth;
+  info[6] = t->chol_ready ? t->chol.nops() : -1;
+  info[7] = t->chol_ready ? t->chol.nwaves : -1;
+  return HLC_OK;
+}
+
+int hlc_tree_perm(const hlc_tree* t, int32_t* perm) {
+  if (!t || !perm) return HLC_ERR_ARG;
+  std::copy(t->T.perm.begin(), t->T.perm.end(), perm);
+  return HLC_OK;
+}
+
+int hlc_tree_leaf_blocks(const hlc_tree* t, int64_t* out) {
+  if (!t || !out) return HLC_ERR_ARG;
+  size_t q = 0;
+  for (int32_t b : t->T.leaves) {
+    const Block& B = t->T.blk[b];
+    out[5 * q + 0] = t->T.cl[B.r].lo;
+    out[5 * q + 1] = t->T.cl[B.r].hi;
+    out[5 * q + 2] = t->T.cl[B.s].lo;
+    out[5 * q + 3] = t->T.cl[B.s].hi;
+    out[5 * q + 4] = B.type;
+    ++q;
+  }
+  return HLC_OK;
+}
+
+int hlc_assemble(hlc_ctx* c, hlc_tree* t, const hlc_theta* th, hlc_hmat** C) {
+  if (!c || !t || !C || t->ctx != c || !valid_theta(th)) return HLC_ERR_ARG;
+  CK(cudaSetDevice(c->device));
+  *C = nullptr;
+  hlc_hmat* M = nullptr;
+  int st = hmat_alloc(t, 0, &M);
+  if (st) return st;
+  st = do_assemble(t, th, M);
+  if (st) {
+    hlc_hmat_free(M);
+    return st;
+  }
+  *C = M;
+  return HLC_OK;
+}
+
+int hlc_cholesky(hlc_ctx* c, const hlc_hmat* C, hlc_hmat** L) {
+  if (!c || !C || !L || C->which != 0 || C->t->ctx != c) return HLC_ERR_ARG;
+  if (!C->valid) return HLC_ERR_STATE;
+  CK(cudaSetDevice(c->device));
+  *L = nullptr;
+  hlc_hmat* M = nullptr;
+  int st = hmat_alloc(C->t, 1, &M);
+  if (st) return st;
+  st = do_cholesky(C->t, C, M);
+  if (st) {
+    hlc_hmat_free(M);
+    return st;
+  }
+  *L = M;
+  return HLC_OK;
+}
+
+int hlc_matvec(hlc_ctx* c, const hlc_hmat* C, const double* x, double* y) {
+  if (!c || !C || !x || !y || C->which != 0 || C->t->ctx != c) return HLC_ERR_ARG;
+  if (!C->valid) return HLC_ERR_STATE;
+  hlc_tree* t = C->t;
+  CK(cudaSetDevice(c->device));
+  int st = build_plans(t, false, true);
+  if (st) return st;
+  const int64_t n = t->T.n;
+  double* X = t->d_vec + n;
+  double* Y = t->d_vec + 2 * n;
+  double* S = t->d_vec + 3 * n;  // staging
+  const bool dx = is_device_ptr(x), dy = is_device_ptr(y);
+  if (dx) {
+    launch_gather(x, t->d_perm, X, n, c->stream);
+  } else {
+    CK(cudaMemcpyAsync(S, x, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    launch_gather(S, t->d_perm, X, n, c->stream);
+  }
+  CK(cudaMemsetAsync(Y, 0, n * sizeof(double), c->stream));
+  Bases B = make_bases(t, nullptr, C->arena, C->ranks);
+  run_plan(t, t->mv, B, c->stream);
+  if (dy) {
+    launch_scatter(Y, t->d_perm, y, n, c->stream);
+  } else {
+    launch_scatter(Y, t->d_perm, S, n, c->stream);
+    CK(cudaMemcpyAsync(y, S, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return take_status(c);
+}
+
+int hlc_hmat_expand(hlc_ctx* c, const hlc_hmat* M, double* out) {
+  if (!c || !M || !out) return HLC_ERR_ARG;
+  hlc_tree* t = M->t;
+  const int64_t n = t->T.n;
+  if (n > 16384) return HLC_ERR_ARG;
+  if (!M->valid) return HLC_ERR_STATE;
+  CK(cudaSetDevice(c->device));
+  std::vector<double> ar(t->T.arena_doubles);
+  std::vector<int> rk(t->T.nslots);
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy(ar.data(), M->arena, ar.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  if (!rk.empty()) CK(cudaMemcpy(rk.data(), M->ranks, rk.size() * sizeof(int), cudaMemcpyDeviceToHost));
+  std::fill(out, out + n * n, 0.0);
+  for (int32_t b : t->T.leaves) {
+    const Block& B = t->T.blk[b];
+    const int64_t r0 = t->T.cl[B.r].lo, c0 = t->T.cl[B.s].lo;
+    for (int64_t j = 0; j < B.n; ++j)
+      for (int64_t i = 0; i < B.m; ++i) {
+        double v = 0.0;
+        if (B.type == BT_DENSE) {
+          v = ar[B.offD + i + j * B.m];
+        } else {
+          const int k = rk[B.slot];
+          for (int l = 0; l < k; ++l) v += ar[B.offU + i + (int64_t)l * B.m] * ar[B.offV + j + (int64_t)l * B.n];
+        }
+        if (M->which == 1 && B.diag && j > i) v = 0.0;
+        const int64_t ui = t->T.perm[r0 + i], uj = t->T.perm[c0 + j];
+        out[ui + uj * n] = v;
+        if (M->which == 0 && (r0 + i) != (c0 + j)) out[uj + ui * n] = v;
+      }
+  }
+  return HLC_OK;
+}
+
+int hlc_hmat_ranks(hlc_ctx* c, const hlc_hmat* M, int32_t* out) {
+  if (!c || !M || !out) return HLC_ERR_ARG;
+  hlc_tree* t = M->t;
+  CK(cudaSetDevice(c->device));
+  std::vector<int> rk(t->T.nslots);
+  CK(cudaStreamSynchronize(c->stream));
+  if (!rk.empty()) CK(cudaMemcpy(rk.data(), M->ranks, rk.size() * sizeof(int), cudaMemcpyDeviceToHost));
+  size_t q = 0;
+  for (int32_t b : t->T.leaves) {
+    const Block& B = t->T.blk[b];
+    out[q++] = B.type == BT_DENSE ? -1 : rk[B.slot];
+  }
+  return HLC_OK;
+}
+
+void hlc_hmat_free(hlc_hmat* M) {
+  if (!M) return;
+  cudaFree(M->arena);
+  cudaFree(M->ranks);
+  delete M;
+}
+
+int hlc_loglik(hlc_ctx* c, hlc_tree* t, const hlc_theta* th, const double* z, hlc_result* out) {
+  if (!c || !t || !z || !out || t->ctx != c || !valid_theta(th)) return HLC_ERR_ARG;
+  CK(cudaSetDevice(c->device));
+  std::memset(out, 0, sizeof(*out));
+  int st = build_plans(t, true, true);
+  if (st) return st;
+  if (!t->wsC && (st = hmat_alloc(t, 0, &t->wsC))) return st;
+  if (!t->wsL && (st = hmat_alloc(t, 1, &t->wsL))) return st;
+  const int64_t n = t->T.n;
+  cudaStream_t s = c->stream;
+  double* W0 = t->d_vec;
+  double* X = t->d_vec + n;
+  double* Y = t->d_vec + 2 * n;
+  double* Z = t->d_vec + 3 * n;
+  double* XS = t->d_vec + 4 * n;
+  // data vector to tree order
+  if (is_device_ptr(z)) {
+    launch_gather(z, t->d_perm, Z, n, s);
+  } else {
+    CK(cudaMemcpyAsync(Y, z, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_gather(Y, t->d_perm, Z, n, s);
+  }
+  CK(cudaEventRecord(c->ev[0], s));
+  if ((st = do_assemble(t, th, t->wsC))) return st;
+  CK(cudaEventRecord(c->ev[1], s));
+  if ((st = do_cholesky(t, t->wsC, t->wsL))) return st;
+  CK(cudaEventRecord(c->ev[2], s));
+  Bases BL = make_bases(t, t->wsL->arena, nullptr, t->wsL->ranks);
+  Bases BC = make_bases(t, nullptr, t->wsC->arena, t->wsC->ranks);
+  // log det = 2 sum log L_ii
+  launch_logdet(t->d_diag_off, t->d_diag_dim, t->ndiag, t->wsL->arena, c->d_part, c->d_scalar + 0, s);
+  // v = L^-1 z, quad_factor = v^T v, x = L^-T v
+  CK(cudaMemcpyAsync(W0, Z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  run_plan(t, t->fwd, BL, s);
+  launch_dot(W0, W0, n, c->d_part, c->d_scalar + 1, s);
+  run_plan(t, t->bwd, BL, s);
+  CK(cudaMemcpyAsync(XS, W0, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  launch_dot(Z, Z, n, c->d_part, c->d_scalar + 2, s);
+  const double logdet_half = read_scalar(c, 0);
+  const double qf = read_scalar(c, 1);
+  const double zn = sqrt(read_scalar(c, 2));
+  // FP64 refinement against C~: x += (L L^T)^-1 (z - C~ x)
+  int it = 0;
+  double rel = 0.0;
+  for (;;) {
+    CK(cudaMemcpyAsync(X, XS, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(Y, 0, n * sizeof(double), s));
+    run_plan(t, t->mv, BC, s);
+    launch_sub(Z, Y, W0, n, s);
+    launch_dot(W0, W0, n, c->d_part, c->d_scalar + 3, s);
+    rel = zn > 0.0 ? sqrt(read_scalar(c, 3)) / zn : 0.0;
+    if (!(rel > t->p.refine_tol) || it >= t->p.refine_maxit) break;
+    run_plan(t, t->fwd, BL, s);
+    run_plan(t, t->bwd, BL, s);
+    launch_axpby(1.0, W0, 1.0, XS, n, s);
+    ++it;
+  }
+  launch_dot(Z, XS, n, c->d_part, c->d_scalar + 4, s);
+  const double quad = read_scalar(c, 4);
+  CK(cudaEventRecord(c->ev[3], s));
+  CK(cudaEventSynchronize(c->ev[3]));
+  if ((st = take_status(c))) return st;
+  float ms[3];
+  cudaEventElapsedTime(&ms[0], c->ev[0], c->ev[1]);
+  cudaEventElapsedTime(&ms[1], c->ev[1], c->ev[2]);
+  cudaEventElapsedTime(&ms[2], c->ev[2], c->ev[3]);
+  const double logdet = 2.0 * logdet_half;
+  if (!(logdet == logdet) || !(quad == quad)) return HLC_ERR_NUMERIC;
+  out->logdet = logdet;
+  out->quad = quad;
+  out->quad_factor = qf;
+  out->loglik = -0.5 * (double)n * log(2.0 * M_PI) - 0.5 * logdet - 0.5 * quad;
+  out->refine_iters = it;
+  out->rel_residual = rel;
+  out->ms_assemble = ms[0];
+  out->ms_factor = ms[1];
+  out->ms_solve = ms[2];
+  hmat_stats(t, t->wsC, &out->bytes_C, &out->max_rank_C);
+  hmat_stats(t, t->wsL, &out->bytes_L, &out->max_rank_L);
+  return HLC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,1086 @@
+// engine.cpp -- host side of the library: tree structures, storage layout and
+// the planner that turns the recursive H-arithmetic into a wave-ordered op
+// program executed by the batched kernels.
+//
+// The planner walks the recursion of the H-Cholesky factorisation (Table 1:
+// truncated addition and multiply-add, the Cholesky of eq. 2) symbolically:
+// it touches no numbers, only block structure, and emits primitive ops
+// (dense POTRF, dense TRSM, strided GEMM, low-rank truncation) with the
+// ranks of low-rank blocks left as runtime values read by the kernels.
+// Every op is placed in the earliest wave after the ops it depends on
+// (read-after-write, write-after-read and write-after-write on 2-D regions of
+// the block storage), so each wave is a set of independent ops that run as
+// one launch per op type.
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <queue>
+#include <stdexcept>
+
+#include "engine.h"
+
+namespace hlc {
+
+// ---------------------------------------------------------------------------
+// Tree construction on the host (used to validate the device tree build and
+// as the structure the planner walks).
+// ---------------------------------------------------------------------------
+static uint64_t interleave32(uint32_t qx, uint32_t qy) {
+  uint64_t k = 0;
+  for (int b = 0; b < 32; ++b) {
+    k |= (uint64_t)((qx >> b) & 1u) << (2 * b);
+    k |= (uint64_t)((qy >> b) & 1u) << (2 * b + 1);
+  }
+  return k;
+}
+
+static uint32_t quantise(double c, double lo, double hi) {
+  const double range = hi - lo;
+  if (!(range > 0.0)) return 0u;
+  const double t = (c - lo) / range * 4294967295.0;
+  return (uint32_t)std::floor(t);
+}
+
+void tree_from_points(HTree& T, const double* x, const double* y, int64_t n, int leaf, double eta) {
+  T.n = n;
+  T.leaf = leaf;
+  T.eta = eta;
+  double lo[2] = {INFINITY, INFINITY}, hi[2] = {-INFINITY, -INFINITY};
+  for (int64_t i = 0; i < n; ++i) {
+    lo[0] = std::min(lo[0], x[i]);
+    hi[0] = std::max(hi[0], x[i]);
+    lo[1] = std::min(lo[1], y[i]);
+    hi[1] = std::max(hi[1], y[i]);
+  }
+  std::vector<std::pair<uint64_t, int32_t>> kv(n);
+  for (int64_t i = 0; i < n; ++i)
+    kv[i] = {interleave32(quantise(x[i], lo[0], hi[0]), quantise(y[i], lo[1], hi[1])), (int32_t)i};
+  std::sort(kv.begin(), kv.end());
+  std::vector<int32_t> idx(n);
+  for (int64_t i = 0; i < n; ++i) idx[i] = kv[i].second;
+
+  // level-by-level bisection; children are appended in order, so clusters
+  // are numbered breadth-first with increasing lo inside a level.
+  T.cl.clear();
+  Cluster root{};
+  root.lo = 0;
+  root.hi = n;
+  root.child[0] = root.child[1] = -1;
+  root.level = 0;
+  T.cl.push_back(root);
+  std::vector<int32_t> frontier{0}, next;
+  std::vector<int32_t> tmp;
+  T.depth = 0;
+  while (!frontier.empty()) {
+    next.clear();
+    for (int32_t c : frontier) {
+      Cluster& C = T.cl[c];
+      C.bmin[0] = C.bmin[1] = INFINITY;
+      C.bmax[0] = C.bmax[1] = -INFINITY;
+      for (int64_t i = C.lo; i < C.hi; ++i) {
+        const double px = x[idx[i]], py = y[idx[i]];
+        C.bmin[0] = std::min(C.bmin[0], px);
+        C.bmax[0] = std::max(C.bmax[0], px);
+        C.bmin[1] = std::min(C.bmin[1], py);
+        C.bmax[1] = std::max(C.bmax[1], py);
+      }
+      T.depth = std::max(T.depth, C.level);
+      if (C.size() <= leaf) continue;
+      const double ex = C.bmax[0] - C.bmin[0], ey = C.bmax[1] - C.bmin[1];
+      const int ax = ex >= ey ? 0 : 1;
+      const double mid = 0.5 * (C.bmin[ax] + C.bmax[ax]);
+      const double* co = ax == 0 ? x : y;
+      tmp.clear();
+      int64_t nl = 0;
+      for (int64_t i = C.lo; i < C.hi; ++i)
+        if (co[idx[i]] <= mid) ++nl;
+      if (nl == 0 || nl == C.size()) continue;  // all points coincide on the axis
+      tmp.reserve(C.size());
+      for (int64_t i = C.lo; i < C.hi; ++i)
+        if (co[idx[i]] <= mid) tmp.push_back(idx[i]);
+      for (int64_t i = C.lo; i < C.hi; ++i)
+        if (!(co[idx[i]] <= mid)) tmp.push_back(idx[i]);
+      std::copy(tmp.begin(), tmp.end(), idx.begin() + C.lo);
+      Cluster a{}, b{};
+      a.lo = C.lo;
+      a.hi = C.lo + nl;
+      b.lo = C.lo + nl;
+      b.hi = C.hi;
+      a.level = b.level = C.level + 1;
+      a.child[0] = a.child[1] = b.child[0] = b.child[1] = -1;
+      const int32_t ia = (int32_t)T.cl.size();
+      T.cl.push_back(a);
+      T.cl.push_back(b);
+      T.cl[c].child[0] = ia;
+      T.cl[c].child[1] = ia + 1;
+      next.push_back(ia);
+      next.push_back(ia + 1);
+    }
+    frontier.swap(next);
+  }
+  T.perm = idx;
+  T.px.resize(n);
+  T.py.resize(n);
+  for (int64_t i = 0; i < n; ++i) {
+    T.px[i] = x[idx[i]];
+    T.py[i] = y[idx[i]];
+  }
+}
+
+static double diam(const Cluster& c) {
+  const double ex = c.bmax[0] - c.bmin[0], ey = c.bmax[1] - c.bmin[1];
+  return std::sqrt(ex * ex + ey * ey);
+}
+
+static double dist(const Cluster& a, const Cluster& b) {
+  double d2 = 0.0;
+  for (int d = 0; d < 2; ++d) {
+    const double g = std::max(0.0, std::max(a.bmin[d] - b.bmax[d], b.bmin[d] - a.bmax[d]));
+    d2 += g * g;
+  }
+  return std::sqrt(d2);
+}
+
+bool is_admissible(const HTree& T, int r, int s) {
+  const double d = dist(T.cl[r], T.cl[s]);
+  if (!(d > 0.0)) return false;
+  return std::min(diam(T.cl[r]), diam(T.cl[s])) <= T.eta * d;
+}
+
+static int32_t build_block(HTree& T, int32_t r, int32_t s) {
+  const int32_t id = (int32_t)T.blk.size();
+  Block b{};
+  b.r = r;
+  b.s = s;
+  b.diag = (r == s);
+  for (int q = 0; q < 4; ++q) b.ch[q] = -1;
+  b.m = T.cl[r].size();
+  b.n = T.cl[s].size();
+  b.slot = -1;
+  b.leaf_index = -1;
+  T.blk.push_back(b);
+  const Cluster cr = T.cl[r], cs = T.cl[s];
+  if (r == s) {
+    if (cr.leaf()) {
+      T.blk[id].type = BT_DENSE;
+    } else {
+      T.blk[id].type = BT_SUB;
+      const int32_t a = build_block(T, cr.child[0], cr.child[0]);
+      const int32_t c = build_block(T, cr.child[1], cr.child[0]);
+      const int32_t d = build_block(T, cr.child[1], cr.child[1]);
+      T.blk[id].ch[0] = a;
+      T.blk[id].ch[2] = c;
+      T.blk[id].ch[3] = d;
+    }
+  } else if (is_admissible(T, r, s)) {
+    T.blk[id].type = BT_LR;
+  } else if (cr.leaf() || cs.leaf()) {
+    T.blk[id].type = BT_DENSE;
+  } else {
+    T.blk[id].type = BT_SUB;
+    int32_t kids[4];
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j) kids[2 * i + j] = build_block(T, cr.child[i], cs.child[j]);
+    for (int q = 0; q < 4; ++q) T.blk[id].ch[q] = kids[q];
+  }
+  return id;
+}
+
+static void collect_leaves(HTree& T, int32_t b) {
+  Block& B = T.blk[b];
+  if (B.type != BT_SUB) {
+    B.leaf_index = (int32_t)T.leaves.size();
+    T.leaves.push_back(b);
+    return;
+  }
+  for (int q = 0; q < 4; ++q)
+    if (T.blk[b].ch[q] >= 0) collect_leaves(T, T.blk[b].ch[q]);
+}
+
+void block_tree(HTree& T) {
+  T.blk.clear();
+  T.leaves.clear();
+  build_block(T, 0, 0);
+  collect_leaves(T, 0);
+}
+
+void layout(HTree& T, int kmax) {
+  T.kmax = kmax;
+  int64_t off = 0;
+  int32_t slots = 0;
+  T.dense_asm.clear();
+  T.lr_asm.clear();
+  T.max_dense_dim = 0;
+  for (int32_t b : T.leaves) {
+    Block& B = T.blk[b];
+    const Cluster& cr = T.cl[B.r];
+    const Cluster& cs = T.cl[B.s];
+    if (B.type == BT_DENSE) {
+      B.offD = off;
+      off += B.m * B.n;
+      off = (off + 3) & ~int64_t(3);  // 32-byte alignment of every block
+      T.dense_asm.push_back(DenseAsm{B.offD, cr.lo, cs.lo, (int32_t)B.m, (int32_t)B.n});
+      T.max_dense_dim = std::max<int64_t>(T.max_dense_dim, std::max(B.m, B.n));
+    } else {
+      B.kcap = (int32_t)std::min<int64_t>(kmax, std::min(B.m, B.n));
+      B.slot = slots++;
+      B.offU = off;
+      off += B.m * B.kcap;
+      off = (off + 3) & ~int64_t(3);
+      B.offV = off;
+      off += B.n * B.kcap;
+      off = (off + 3) & ~int64_t(3);
+      T.lr_asm.push_back(LrAsm{B.offU, B.offV, cr.lo, cs.lo, (int32_t)B.m, (int32_t)B.n, B.kcap, B.slot});
+    }
+  }
+  T.arena_doubles = off;
+  T.nslots = slots;
+}
+
+// ---------------------------------------------------------------------------
+// Planner
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Rect {
+  int64_t r0, r1, c0, c1;
+  bool overlaps(const Rect& o) const { return r0 < o.r1 && o.r0 < r1 && c0 < o.c1 && o.c0 < c1; }
+  bool operator==(const Rect& o) const { return r0 == o.r0 && r1 == o.r1 && c0 == o.c0 && c1 == o.c1; }
+};
+
+struct Acc {
+  Rect rc;
+  int32_t lw, lr;  // wave of the last write / latest read
+};
+
+struct Obj {
+  int32_t buf;
+  int64_t off, ld;
+  std::vector<Acc> acc;
+  // temporaries: size, lifetime in waves, rows already written (union)
+  int64_t size = 0;
+  int32_t birth = INT32_MAX, death = -1;
+  std::vector<std::pair<int64_t, int64_t>> written;
+};
+
+// A view in storage coordinates of an object: element (i, j) of the view is
+// storage element (sr + i, sc + j), or (sr + j, sc + i) when transposed.
+struct PV {
+  int32_t obj;
+  int64_t sr, sc;
+  int64_t rows, cols;  // static extents (capacities)
+  bool tr;
+  int32_t drow, dcol;  // rank slot of a dynamic extent, -1 if static
+};
+
+const int32_t NOSLOT = -1;
+
+struct Planner {
+  HTree& T;
+  Plan& P;
+  int32_t mat_buf;
+  std::vector<Obj> objs;
+  std::vector<int32_t> objD, objU, objV;  // per block id
+  int64_t tmp_top = 0;
+  struct Ref {
+    int32_t type;
+    int64_t idx;
+    int32_t wave;
+  };
+  std::vector<Ref> seq;
+  int32_t maxwave = -1;
+
+  Planner(HTree& t, Plan& p, int32_t mbuf) : T(t), P(p), mat_buf(mbuf) {
+    objD.assign(T.blk.size(), -1);
+    objU.assign(T.blk.size(), -1);
+    objV.assign(T.blk.size(), -1);
+    for (int32_t b : T.leaves) {
+      const Block& B = T.blk[b];
+      if (B.type == BT_DENSE) {
+        objD[b] = add_obj(mat_buf, B.offD, B.m);
+      } else {
+        objU[b] = add_obj(mat_buf, B.offU, B.m);
+        objV[b] = add_obj(mat_buf, B.offV, B.n);
+      }
+    }
+  }
+
+  int32_t add_obj(int32_t buf, int64_t off, int64_t ld) {
+    Obj o;
+    o.buf = buf;
+    o.off = off;
+    o.ld = ld;
+    objs.push_back(std::move(o));
+    return (int32_t)objs.size() - 1;
+  }
+
+  // Temporaries get a virtual offset here; finish() maps them onto reused
+  // physical storage according to their lifetimes.
+  std::vector<int32_t> tmp_objs;
+  int32_t new_tmp(int64_t rows, int64_t cols) {
+    const int64_t off = tmp_top;
+    const int64_t sz = ((std::max<int64_t>(rows * cols, 1)) + 3) & ~int64_t(3);
+    tmp_top += sz;
+    const int32_t o = add_obj(BUF_TMP, off, std::max<int64_t>(rows, 1));
+    objs[o].size = sz;
+    tmp_objs.push_back(o);
+    return o;
+  }
+
+  // beta for a write of rows [a, b) into a temporary: 0 when nothing of it
+  // was written before, 1 when all of it was; a partial overlap cannot
+  // arise for cluster-aligned row ranges and is rejected.
+  int32_t first_write_beta(const PV& v) {
+    Obj& o = objs[v.obj];
+    if (o.buf != BUF_TMP) return 1;
+    const Rect rc = rect(v);
+    const int64_t a = rc.r0, b = rc.r1;
+    int64_t cov = 0;
+    for (auto& iv : o.written) cov += std::max<int64_t>(0, std::min(b, iv.second) - std::max(a, iv.first));
+    if (cov != 0 && cov != b - a) throw std::runtime_error("planner: partial first write of a temporary");
+    if (cov == 0) {
+      // merge [a, b) into the union
+      o.written.push_back({a, b});
+      std::sort(o.written.begin(), o.written.end());
+      std::vector<std::pair<int64_t, int64_t>> mg;
+      for (auto& iv : o.written) {
+        if (!mg.empty() && iv.first <= mg.back().second)
+          mg.back().second = std::max(mg.back().second, iv.second);
+        else
+          mg.push_back(iv);
+      }
+      o.written.swap(mg);
+      return 0;
+    }
+    return 1;
+  }
+
+  // ---- views ----
+  PV whole(int32_t obj, int64_t rows, int64_t cols, int32_t drow = NOSLOT, int32_t dcol = NOSLOT) {
+    return PV{obj, 0, 0, rows, cols, false, drow, dcol};
+  }
+  static PV T_(const PV& v) {
+    PV t = v;
+    t.tr = !v.tr;
+    t.rows = v.cols;
+    t.cols = v.rows;
+    t.drow = v.dcol;
+    t.dcol = v.drow;
+    return t;
+  }
+  static PV rows(const PV& v, int64_t a, int64_t b) {
+    PV t = v;
+    if (!v.tr)
+      t.sr += a;
+    else
+      t.sc += a;
+    t.rows = b - a;
+    t.drow = NOSLOT;
+    return t;
+  }
+  static PV cols(const PV& v, int64_t a, int64_t b) {
+    PV t = v;
+    if (!v.tr)
+      t.sc += a;
+    else
+      t.sr += a;
+    t.cols = b - a;
+    t.dcol = NOSLOT;
+    return t;
+  }
+  Rect rect(const PV& v) const {
+    if (!v.tr) return Rect{v.sr, v.sr + v.rows, v.sc, v.sc + v.cols};
+    return Rect{v.sr, v.sr + v.cols, v.sc, v.sc + v.rows};
+  }
+  Mv mv(const PV& v) const {
+    const Obj& o = objs[v.obj];
+    Mv m;
+    m.buf = o.buf;
+    m.pad = 0;
+    m.off = o.off + v.sr + v.sc * o.ld;
+    m.rs = v.tr ? o.ld : 1;
+    m.cs = v.tr ? 1 : o.ld;
+    return m;
+  }
+  static Dim dim(int64_t n, int32_t slot) { return Dim{(int32_t)n, slot}; }
+
+  // ---- dependency analysis ----
+  int32_t place(const std::vector<PV>& reads, const std::vector<PV>& writes) {
+    int32_t w = 0;
+    for (const PV& v : reads) {
+      if (v.rows <= 0 || v.cols <= 0) continue;
+      const Rect rc = rect(v);
+      for (const Acc& a : objs[v.obj].acc)
+        if (a.rc.overlaps(rc)) w = std::max(w, a.lw + 1);
+    }
+    for (const PV& v : writes) {
+      if (v.rows <= 0 || v.cols <= 0) continue;
+      const Rect rc = rect(v);
+      for (const Acc& a : objs[v.obj].acc)
+        if (a.rc.overlaps(rc)) w = std::max(w, std::max(a.lw, a.lr) + 1);
+    }
+    for (const PV& v : reads) {
+      if (v.rows <= 0 || v.cols <= 0) continue;
+      Obj& ob = objs[v.obj];
+      if (ob.buf == BUF_TMP) {
+        ob.birth = std::min(ob.birth, w);
+        ob.death = std::max(ob.death, w);
+      }
+      const Rect rc = rect(v);
+      bool found = false;
+      for (Acc& a : objs[v.obj].acc)
+        if (a.rc == rc) {
+          a.lr = std::max(a.lr, w);
+          found = true;
+          break;
+        }
+      if (!found) objs[v.obj].acc.push_back(Acc{rc, -1, w});
+    }
+    for (const PV& v : writes) {
+      if (v.rows <= 0 || v.cols <= 0) continue;
+      Obj& ob = objs[v.obj];
+      if (ob.buf == BUF_TMP) {
+        ob.birth = std::min(ob.birth, w);
+        ob.death = std::max(ob.death, w);
+      }
+      const Rect rc = rect(v);
+      std::vector<Acc>& L = objs[v.obj].acc;
+      // accesses covered by this write are superseded by it
+      L.erase(std::remove_if(L.begin(), L.end(),
+                             [&](const Acc& a) {
+                               return a.rc.r0 >= rc.r0 && a.rc.r1 <= rc.r1 && a.rc.c0 >= rc.c0 &&
+                                      a.rc.c1 <= rc.c1;
+                             }),
+              L.end());
+      L.push_back(Acc{rc, w, -1});
+    }
+    maxwave = std::max(maxwave, w);
+    return w;
+  }
+
+  // ---- op emission ----
+  void gemm(const PV& Y, const PV& A, const PV& B, Dim m, Dim k, Dim c, double alpha) {
+    if (m.n <= 0 || c.n <= 0 || k.n <= 0) return;
+    OpGemm op;
+    op.Y = mv(Y);
+    op.A = mv(A);
+    op.B = mv(B);
+    op.m = m;
+    op.k = k;
+    op.c = c;
+    op.alpha = alpha;
+    op.beta = first_write_beta(Y);
+    op.pad = 0;
+    const int32_t w = place({A, B}, {Y});
+    P.gemm.push_back(op);
+    seq.push_back(Ref{OP_GEMM, (int64_t)P.gemm.size() - 1, w});
+  }
+  // Y += alpha * X (B marked as the identity)
+  void axpy(const PV& Y, const PV& X, Dim m, Dim c, double alpha) {
+    if (m.n <= 0 || c.n <= 0) return;
+    OpGemm op;
+    op.Y = mv(Y);
+    op.A = mv(X);
+    op.B = Mv{0, 0, 0, -1, 0};
+    op.m = m;
+    op.k = c;
+    op.c = c;
+    op.alpha = alpha;
+    op.beta = first_write_beta(Y);
+    op.pad = 0;
+    const int32_t w = place({X}, {Y});
+    P.gemm.push_back(op);
+    seq.push_back(Ref{OP_GEMM, (int64_t)P.gemm.size() - 1, w});
+  }
+  void trsm(const PV& L, const PV& X, int64_t n, int trans, Dim c) {
+    if (n <= 0 || c.n <= 0) return;
+    OpTrsm op;
+    op.L = mv(L);
+    op.X = mv(X);
+    op.n = (int32_t)n;
+    op.trans = trans;
+    op.c = c;
+    const int32_t w = place({L}, {X});
+    P.trsm.push_back(op);
+    seq.push_back(Ref{OP_TRSM, (int64_t)P.trsm.size() - 1, w});
+  }
+  void potrf(int32_t b) {
+    const Block& B = T.blk[b];
+    OpPotrf op;
+    PV A = whole(objD[b], B.m, B.n);
+    op.A = mv(A);
+    op.n = (int32_t)B.m;
+    op.row0 = (int32_t)T.cl[B.r].lo;
+    const int32_t w = place({}, {A});
+    P.potrf.push_back(op);
+    seq.push_back(Ref{OP_POTRF, (int64_t)P.potrf.size() - 1, w});
+  }
+
+  struct TermP {
+    PV U, V;
+    int64_t urows, vrows;
+    int64_t roff, coff;
+    Dim k;
+    int32_t flags;
+    double alpha;
+  };
+
+  void trunc(int32_t b, const std::vector<TermP>& terms, int keep) {
+    const Block& B = T.blk[b];
+    OpTrunc op;
+    PV U = whole(objU[b], B.m, B.kcap), V = whole(objV[b], B.n, B.kcap);
+    op.U = mv(U);
+    op.V = mv(V);
+    op.m = (int32_t)B.m;
+    op.n = (int32_t)B.n;
+    op.kcap = B.kcap;
+    op.slot = B.slot;
+    op.nterms = (int32_t)terms.size();
+    op.keep = keep;
+    op.term0 = (int64_t)P.terms.size();
+    op.eps = T.eps;
+    std::vector<PV> reads;
+    for (const TermP& t : terms) {
+      TermD d;
+      d.U = (t.flags & 1) ? Mv{0, 0, 0, -1, 0} : mv(t.U);
+      d.V = (t.flags & 2) ? Mv{0, 0, 0, -1, 0} : mv(t.V);
+      d.urows = (int32_t)t.urows;
+      d.vrows = (int32_t)t.vrows;
+      d.roff = (int32_t)t.roff;
+      d.coff = (int32_t)t.coff;
+      d.k = t.k;
+      d.flags = t.flags;
+      d.pad = 0;
+      d.alpha = t.alpha;
+      P.terms.push_back(d);
+      if (!(t.flags & 1)) reads.push_back(t.U);
+      if (!(t.flags & 2)) reads.push_back(t.V);
+    }
+    const int32_t w = place(reads, {U, V});
+    P.trunc.push_back(op);
+    seq.push_back(Ref{OP_TRUNC, (int64_t)P.trunc.size() - 1, w});
+  }
+
+  // ---- block views ----
+  const Block& blk(int32_t b) const { return T.blk[b]; }
+  int64_t rlo(int32_t b) const { return T.cl[T.blk[b].r].lo; }
+  int64_t slo(int32_t b) const { return T.cl[T.blk[b].s].lo; }
+  PV D(int32_t b) { return whole(objD[b], blk(b).m, blk(b).n); }
+  PV U(int32_t b) { return whole(objU[b], blk(b).m, blk(b).kcap, NOSLOT, blk(b).slot); }
+  PV V(int32_t b) { return whole(objV[b], blk(b).n, blk(b).kcap, NOSLOT, blk(b).slot); }
+  Dim rk(int32_t b) { return dim(blk(b).kcap, blk(b).slot); }
+
+  // ---- H-arithmetic (mirrors the recursion of the H-Cholesky) ----
+
+  // Y += alpha * A X  (A off-diagonal)
+  void hmul(int32_t a, const PV& X, const PV& Y, double alpha) {
+    const Block& A = blk(a);
+    const Dim c = dim(X.cols, X.dcol);
+    if (A.type == BT_DENSE) {
+      gemm(Y, D(a), X, dim(A.m, NOSLOT), dim(A.n, NOSLOT), c, alpha);
+    } else if (A.type == BT_LR) {
+      const int32_t t = new_tmp(A.kcap, X.cols);
+      PV Tv = whole(t, A.kcap, X.cols, A.slot, X.dcol);
+      gemm(Tv, T_(V(a)), X, rk(a), dim(A.n, NOSLOT), c, 1.0);
+      gemm(Y, U(a), Tv, dim(A.m, NOSLOT), rk(a), c, alpha);
+    } else {
+      const int64_t r0 = rlo(a), s0 = slo(a);
+      for (int q = 0; q < 4; ++q) {
+        const int32_t cb = A.ch[q];
+        if (cb < 0) continue;
+        const Cluster& cr = T.cl[blk(cb).r];
+        const Cluster& cs = T.cl[blk(cb).s];
+        hmul(cb, rows(X, cs.lo - s0, cs.hi - s0), rows(Y, cr.lo - r0, cr.hi - r0), alpha);
+      }
+    }
+  }
+
+  // Y += alpha * A^T X  (A off-diagonal)
+  void hmul_t(int32_t a, const PV& X, const PV& Y, double alpha) {
+    const Block& A = blk(a);
+    const Dim c = dim(X.cols, X.dcol);
+    if (A.type == BT_DENSE) {
+      gemm(Y, T_(D(a)), X, dim(A.n, NOSLOT), dim(A.m, NOSLOT), c, alpha);
+    } else if (A.type == BT_LR) {
+      const int32_t t = new_tmp(A.kcap, X.cols);
+      PV Tv = whole(t, A.kcap, X.cols, A.slot, X.dcol);
+      gemm(Tv, T_(U(a)), X, rk(a), dim(A.m, NOSLOT), c, 1.0);
+      gemm(Y, V(a), Tv, dim(A.n, NOSLOT), rk(a), c, alpha);
+    } else {
+      const int64_t r0 = rlo(a), s0 = slo(a);
+      for (int q = 0; q < 4; ++q) {
+        const int32_t cb = A.ch[q];
+        if (cb < 0) continue;
+        const Cluster& cr = T.cl[blk(cb).r];
+        const Cluster& cs = T.cl[blk(cb).s];
+        hmul_t(cb, rows(X, cr.lo - r0, cr.hi - r0), rows(Y, cs.lo - s0, cs.hi - s0), alpha);
+      }
+    }
+  }
+
+  int64_t cut(int32_t l) const {
+    const Cluster& t = T.cl[blk(l).r];
+    return T.cl[t.child[0]].hi - t.lo;
+  }
+
+  // X := L^-1 X
+  void trsv(int32_t l, const PV& X) {
+    const Block& L = blk(l);
+    if (L.type == BT_DENSE) {
+      trsm(D(l), X, L.m, 0, dim(X.cols, X.dcol));
+      return;
+    }
+    const int64_t c = cut(l);
+    const PV X0 = rows(X, 0, c), X1 = rows(X, c, X.rows);
+    trsv(L.ch[0], X0);
+    hmul(L.ch[2], X0, X1, -1.0);
+    trsv(L.ch[3], X1);
+  }
+
+  // X := L^-T X
+  void trsv_t(int32_t l, const PV& X) {
+    const Block& L = blk(l);
+    if (L.type == BT_DENSE) {
+      trsm(D(l), X, L.m, 1, dim(X.cols, X.dcol));
+      return;
+    }
+    const int64_t c = cut(l);
+    const PV X0 = rows(X, 0, c), X1 = rows(X, c, X.rows);
+    trsv_t(L.ch[3], X1);
+    hmul_t(L.ch[2], X1, X0, -1.0);
+    trsv_t(L.ch[0], X0);
+  }
+
+  // C += alpha U V^T
+  void add_lr(int32_t c, const PV& Uv, const PV& Vv, Dim k, double alpha) {
+    const Block& C = blk(c);
+    if (k.n <= 0) return;
+    if (C.type == BT_DENSE) {
+      gemm(D(c), Uv, T_(Vv), dim(C.m, NOSLOT), k, dim(C.n, NOSLOT), alpha);
+    } else if (C.type == BT_LR) {
+      TermP t{Uv, Vv, C.m, C.n, 0, 0, k, 0, alpha};
+      trunc(c, {t}, 1);
+    } else {
+      const int64_t r0 = rlo(c), s0 = slo(c);
+      for (int q = 0; q < 4; ++q) {
+        const int32_t cb = C.ch[q];
+        if (cb < 0) continue;
+        const Cluster& cr = T.cl[blk(cb).r];
+        const Cluster& cs = T.cl[blk(cb).s];
+        add_lr(cb, rows(Uv, cr.lo - r0, cr.hi - r0), rows(Vv, cs.lo - s0, cs.hi - s0), k, alpha);
+      }
+    }
+  }
+
+  // C += P (P a dense |r| x |s| view, already scaled)
+  void add_dense(int32_t c, const PV& Pv) {
+    const Block& C = blk(c);
+    if (C.type == BT_DENSE) {
+      axpy(D(c), Pv, dim(C.m, NOSLOT), dim(C.n, NOSLOT), 1.0);
+    } else if (C.type == BT_LR) {
+      TermP t;
+      t.roff = t.coff = 0;
+      t.alpha = 1.0;
+      t.urows = C.m;
+      t.vrows = C.n;
+      if (C.m <= C.n) {  // P = I (P^T)^T
+        t.U = Pv;
+        t.V = T_(Pv);
+        t.flags = 1;
+        t.k = dim(C.m, NOSLOT);
+      } else {  // P = P I^T
+        t.U = Pv;
+        t.V = Pv;
+        t.flags = 2;
+        t.k = dim(C.n, NOSLOT);
+      }
+      trunc(c, {t}, 1);
+    } else {
+      const int64_t r0 = rlo(c), s0 = slo(c);
+      for (int q = 0; q < 4; ++q) {
+        const int32_t cb = C.ch[q];
+        if (cb < 0) continue;
+        const Cluster& cr = T.cl[blk(cb).r];
+        const Cluster& cs = T.cl[blk(cb).s];
+        add_dense(cb, cols(rows(Pv, cr.lo - r0, cr.hi - r0), cs.lo - s0, cs.hi - s0));
+      }
+    }
+  }
+
+  // exact product A B^T as low-rank terms inside the |r| x |r'| target
+  void prod_terms(int32_t a, int32_t b, int64_t roff, int64_t coff, double alpha, std::vector<TermP>& out) {
+    const Block& A = blk(a);
+    const Block& B = blk(b);
+    if (A.type == BT_LR) {
+      const int32_t w = new_tmp(B.m, A.kcap);
+      PV W = whole(w, B.m, A.kcap, NOSLOT, A.slot);
+      hmul(b, V(a), W, 1.0);
+      out.push_back(TermP{U(a), W, A.m, B.m, roff, coff, rk(a), 0, alpha});
+    } else if (B.type == BT_LR) {
+      const int32_t w = new_tmp(A.m, B.kcap);
+      PV W = whole(w, A.m, B.kcap, NOSLOT, B.slot);
+      hmul(a, V(b), W, 1.0);
+      out.push_back(TermP{W, U(b), A.m, B.m, roff, coff, rk(b), 0, alpha});
+    } else if (A.type == BT_DENSE && B.type == BT_DENSE) {
+      out.push_back(TermP{D(a), D(b), A.m, B.m, roff, coff, dim(A.n, NOSLOT), 0, alpha});
+    } else if (A.type == BT_DENSE) {
+      const int32_t w = new_tmp(B.m, A.m);
+      PV W = whole(w, B.m, A.m);
+      hmul(b, T_(D(a)), W, 1.0);
+      out.push_back(TermP{W, W, A.m, B.m, roff, coff, dim(A.m, NOSLOT), 1, alpha});
+    } else if (B.type == BT_DENSE) {
+      const int32_t w = new_tmp(A.m, B.m);
+      PV W = whole(w, A.m, B.m);
+      hmul(a, T_(D(b)), W, 1.0);
+      out.push_back(TermP{W, W, A.m, B.m, roff, coff, dim(B.m, NOSLOT), 2, alpha});
+    } else {
+      const int64_t ar0 = rlo(a), br0 = rlo(b);
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j)
+          for (int l = 0; l < 2; ++l) {
+            const int32_t ai = A.ch[2 * i + l], bj = B.ch[2 * j + l];
+            prod_terms(ai, bj, roff + rlo(ai) - ar0, coff + rlo(bj) - br0, alpha, out);
+          }
+    }
+  }
+
+  // C += alpha A B^T with truncation; A = (r, s), B = (r', s), C = (r, r')
+  void mul_add(int32_t c, int32_t a, int32_t b, double alpha) {
+    const Block& A = blk(a);
+    const Block& B = blk(b);
+    const Block& C = blk(c);
+    if (A.type == BT_LR) {
+      const int32_t w = new_tmp(B.m, A.kcap);
+      PV W = whole(w, B.m, A.kcap, NOSLOT, A.slot);
+      hmul(b, V(a), W, 1.0);
+      add_lr(c, U(a), W, rk(a), alpha);
+    } else if (B.type == BT_LR) {
+      const int32_t w = new_tmp(A.m, B.kcap);
+      PV W = whole(w, A.m, B.kcap, NOSLOT, B.slot);
+      hmul(a, V(b), W, alpha);
+      add_lr(c, W, U(b), rk(b), 1.0);
+    } else if (A.type == BT_DENSE && B.type == BT_DENSE) {
+      if (C.type == BT_DENSE) {
+        gemm(D(c), D(a), T_(D(b)), dim(C.m, NOSLOT), dim(A.n, NOSLOT), dim(C.n, NOSLOT), alpha);
+      } else {
+        const int32_t p = new_tmp(A.m, B.m);
+        PV Pv = whole(p, A.m, B.m);
+        gemm(Pv, D(a), T_(D(b)), dim(A.m, NOSLOT), dim(A.n, NOSLOT), dim(B.m, NOSLOT), alpha);
+        add_dense(c, Pv);
+      }
+    } else if (A.type == BT_DENSE) {
+      const int32_t w = new_tmp(B.m, A.m);
+      PV W = whole(w, B.m, A.m);
+      hmul(b, T_(D(a)), W, alpha);
+      add_dense(c, T_(W));
+    } else if (B.type == BT_DENSE) {
+      const int32_t w = new_tmp(A.m, B.m);
+      PV W = whole(w, A.m, B.m);
+      hmul(a, T_(D(b)), W, alpha);
+      add_dense(c, W);
+    } else if (C.type == BT_SUB) {
+      const bool dg = C.diag;
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+          if (dg && j > i) continue;
+          const int32_t cc = C.ch[2 * i + j];
+          for (int l = 0; l < 2; ++l) mul_add(cc, A.ch[2 * i + l], B.ch[2 * j + l], alpha);
+        }
+    } else {
+      std::vector<TermP> terms;
+      prod_terms(a, b, 0, 0, alpha, terms);
+      if (C.type == BT_LR) {
+        trunc(c, terms, 1);
+      } else {
+        // not reachable for geometric trees (a dense target has a leaf
+        // cluster); expand the terms into a temporary and add it
+        const int32_t p = new_tmp(C.m, C.n);
+        PV Pv = whole(p, C.m, C.n);
+        for (const TermP& t : terms) {
+          PV Y = cols(rows(Pv, t.roff, t.roff + t.urows), t.coff, t.coff + t.vrows);
+          if (t.flags == 1)
+            axpy(Y, T_(t.V), dim(t.urows, NOSLOT), dim(t.vrows, NOSLOT), t.alpha);
+          else if (t.flags == 2)
+            axpy(Y, t.U, dim(t.urows, NOSLOT), dim(t.vrows, NOSLOT), t.alpha);
+          else
+            gemm(Y, t.U, T_(t.V), dim(t.urows, NOSLOT), t.k, dim(t.vrows, NOSLOT), t.alpha);
+        }
+        add_dense(c, Pv);
+      }
+    }
+  }
+
+  // B := B L^-T
+  void trsm_blk(int32_t l, int32_t b) {
+    const Block& B = blk(b);
+    if (B.type == BT_DENSE) {
+      trsv(l, T_(D(b)));
+    } else if (B.type == BT_LR) {
+      trsv(l, V(b));
+    } else {
+      const Block& L = blk(l);
+      for (int i = 0; i < 2; ++i) {
+        const int32_t b0 = B.ch[2 * i], b1 = B.ch[2 * i + 1];
+        trsm_blk(L.ch[0], b0);
+        mul_add(b1, b0, L.ch[2], -1.0);
+        trsm_blk(L.ch[3], b1);
+      }
+    }
+  }
+
+  void chol(int32_t m) {
+    const Block& M = blk(m);
+    if (M.type == BT_DENSE) {
+      potrf(m);
+      return;
+    }
+    chol(M.ch[0]);
+    trsm_blk(M.ch[0], M.ch[2]);
+    mul_add(M.ch[3], M.ch[2], M.ch[2], -1.0);
+    chol(M.ch[3]);
+  }
+
+  // y += C x for the symmetric matrix stored as lower block triangle
+  void symv(int32_t b, const PV& x, const PV& y) {
+    const Block& B = blk(b);
+    const Cluster& cr = T.cl[B.r];
+    const Cluster& cs = T.cl[B.s];
+    if (B.diag) {
+      if (B.type == BT_DENSE) {
+        gemm(rows(y, cr.lo, cr.hi), D(b), rows(x, cs.lo, cs.hi), dim(B.m, NOSLOT), dim(B.n, NOSLOT),
+             dim(x.cols, NOSLOT), 1.0);
+      } else {
+        symv(B.ch[0], x, y);
+        symv(B.ch[2], x, y);
+        symv(B.ch[3], x, y);
+      }
+      return;
+    }
+    hmul(b, rows(x, cs.lo, cs.hi), rows(y, cr.lo, cr.hi), 1.0);
+    hmul_t(b, rows(x, cr.lo, cr.hi), rows(y, cs.lo, cs.hi), 1.0);
+  }
+
+  // ---- finish: group ops into launches ----
+  // Map the temporaries onto physical storage: a temporary lives from the
+  // first wave that writes it to the last wave that reads it; storage is
+  // reused first-fit once a temporary is dead.
+  void allocate_temps() {
+    std::vector<int32_t> order = tmp_objs;
+    std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+      if (objs[a].birth != objs[b].birth) return objs[a].birth < objs[b].birth;
+      return a < b;
+    });
+    std::map<int64_t, int64_t> freel;  // offset -> size
+    int64_t top = 0;
+    using Live = std::pair<int32_t, int32_t>;  // (death, obj)
+    std::priority_queue<Live, std::vector<Live>, std::greater<Live>> live;
+    std::vector<int64_t> phys(objs.size(), -1);
+    auto release = [&](int64_t off, int64_t sz) {
+      auto it = freel.emplace(off, sz).first;
+      auto nx = std::next(it);
+      if (nx != freel.end() && it->first + it->second == nx->first) {
+        it->second += nx->second;
+        freel.erase(nx);
+      }
+      if (it != freel.begin()) {
+        auto pv = std::prev(it);
+        if (pv->first + pv->second == it->first) {
+          pv->second += it->second;
+          freel.erase(it);
+        }
+      }
+    };
+    for (int32_t o : order) {
+      Obj& ob = objs[o];
+      if (ob.death < 0) {  // never used
+        ob.birth = ob.death = 0;
+      }
+      while (!live.empty() && live.top().first < ob.birth) {
+        const int32_t d = live.top().second;
+        live.pop();
+        release(phys[d], objs[d].size);
+      }
+      int64_t at = -1;
+      for (auto it = freel.begin(); it != freel.end(); ++it)
+        if (it->second >= ob.size) {
+          at = it->first;
+          const int64_t rest = it->second - ob.size;
+          freel.erase(it);
+          if (rest > 0) freel.emplace(at + ob.size, rest);
+          break;
+        }
+      if (at < 0) {
+        at = top;
+        top += ob.size;
+      }
+      phys[o] = at;
+      live.push(Live{ob.death, o});
+    }
+    P.tmp_doubles = top;
+    // virtual -> physical: temporaries are contiguous in virtual space in
+    // creation order
+    std::vector<int64_t> vbase(tmp_objs.size());
+    for (size_t i = 0; i < tmp_objs.size(); ++i) vbase[i] = objs[tmp_objs[i]].off;
+    auto patch = [&](Mv& m) {
+      if (m.buf != BUF_TMP) return;
+      const size_t i = std::upper_bound(vbase.begin(), vbase.end(), m.off) - vbase.begin() - 1;
+      const int32_t o = tmp_objs[i];
+      m.off += phys[o] - objs[o].off;
+    };
+    for (OpGemm& g : P.gemm) {
+      patch(g.Y);
+      patch(g.A);
+      if (g.B.buf >= 0) patch(g.B);
+    }
+    for (OpTrsm& t : P.trsm) {
+      patch(t.L);
+      patch(t.X);
+    }
+    for (TermD& t : P.terms) {
+      if (!(t.flags & 1)) patch(t.U);
+      if (!(t.flags & 2)) patch(t.V);
+    }
+  }
+
+  void finish() {
+    allocate_temps();
+    P.nwaves = maxwave + 1;
+    // stable order by (wave, type)
+    std::vector<int64_t> order(seq.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+      if (seq[a].wave != seq[b].wave) return seq[a].wave < seq[b].wave;
+      return seq[a].type < seq[b].type;
+    });
+    std::vector<OpGemm> g;
+    std::vector<OpTrsm> t;
+    std::vector<OpPotrf> p;
+    std::vector<OpTrunc> u;
+    P.launches.clear();
+    P.max_trunc_per_wave = 0;
+    for (size_t i = 0; i < order.size(); ++i) {
+      const Ref& r = seq[order[i]];
+      int64_t pos = 0;
+      switch (r.type) {
+        case OP_GEMM: pos = (int64_t)g.size(); g.push_back(P.gemm[r.idx]); break;
+        case OP_TRSM: pos = (int64_t)t.size(); t.push_back(P.trsm[r.idx]); break;
+        case OP_POTRF: pos = (int64_t)p.size(); p.push_back(P.potrf[r.idx]); break;
+        default: pos = (int64_t)u.size(); u.push_back(P.trunc[r.idx]); break;
+      }
+      if (!P.launches.empty() && P.launches.back().wave == r.wave && P.launches.back().type == r.type) {
+        P.launches.back().count++;
+      } else {
+        P.launches.push_back(Launch{r.type, r.wave, pos, 1});
+      }
+      if (r.type == OP_TRUNC) P.max_trunc_per_wave = std::max(P.max_trunc_per_wave, P.launches.back().count);
+    }
+    P.gemm.swap(g);
+    P.trsm.swap(t);
+    P.potrf.swap(p);
+    P.trunc.swap(u);
+  }
+};
+
+}  // namespace
+
+void plan_cholesky(HTree& T, Plan& P) {
+  P = Plan();
+  Planner pl(T, P, BUF_L);
+  pl.chol(0);
+  pl.finish();
+}
+
+// Forward (trans = 0) or backward (trans = 1) solve of the factor against
+// the vector(s) in BUF_VEC at offset voff (n x ncols, ld n).
+void plan_solve(HTree& T, Plan& P, int trans, int64_t voff, int64_t ncols) {
+  P = Plan();
+  Planner pl(T, P, BUF_L);
+  const int32_t v = pl.add_obj(BUF_VEC, voff, T.n);
+  PV X = pl.whole(v, T.n, ncols);
+  if (trans)
+    pl.trsv_t(0, X);
+  else
+    pl.trsv(0, X);
+  pl.finish();
+}
+
+// y (BUF_VEC at yoff) += C x (BUF_VEC at xoff); C in BUF_C.
+void plan_matvec(HTree& T, Plan& P, int64_t xoff, int64_t yoff, int64_t ncols) {
+  P = Plan();
+  Planner pl(T, P, BUF_C);
+  const int32_t xo = pl.add_obj(BUF_VEC, xoff, T.n);
+  const int32_t yo = pl.add_obj(BUF_VEC, yoff, T.n);
+  pl.symv(0, pl.whole(xo, T.n, ncols), pl.whole(yo, T.n, ncols));
+  pl.finish();
+}
+
+// Recompression of every assembled low-rank block (in place, BUF_C).
+void plan_recompress(HTree& T, Plan& P) {
+  P = Plan();
+  Planner pl(T, P, BUF_C);
+  for (int32_t b : T.leaves)
+    if (T.blk[b].type == BT_LR) pl.trunc(b, {}, 1);
+  pl.finish();
+}
+
+// Every view of every op must stay inside its buffer at full capacity
+// (static extents, ranks at their caps).  Returns an empty string or the
+// first violation.
+std::string validate_plan(const Plan& P, const int64_t* bufsize) {
+  char msg[256];
+  auto check = [&](const Mv& v, int64_t rows, int64_t cols, const char* what, int64_t i) -> bool {
+    if (rows <= 0 || cols <= 0) return true;
+    if (v.buf < 0 || v.buf >= NBUF || v.off < 0 || v.rs < 0 || v.cs < 0) {
+      snprintf(msg, sizeof msg, "%s op %lld: bad view (buf %d off %lld)", what, (long long)i, v.buf,
+               (long long)v.off);
+      return false;
+    }
+    const int64_t last = v.off + (rows - 1) * v.rs + (cols - 1) * v.cs;
+    if (last >= bufsize[v.buf]) {
+      snprintf(msg, sizeof msg, "%s op %lld: view ends at %lld beyond buffer %d of %lld", what, (long long)i,
+               (long long)last, v.buf, (long long)bufsize[v.buf]);
+      return false;
+    }
+    return true;
+  };
+  for (size_t i = 0; i < P.gemm.size(); ++i) {
+    const OpGemm& g = P.gemm[i];
+    if (!check(g.Y, g.m.n, g.c.n, "gemm.Y", i)) return msg;
+    if (g.B.buf < 0) {
+      if (!check(g.A, g.m.n, g.c.n, "axpy.X", i)) return msg;
+    } else {
+      if (!check(g.A, g.m.n, g.k.n, "gemm.A", i) || !check(g.B, g.k.n, g.c.n, "gemm.B", i)) return msg;
+    }
+  }
+  for (size_t i = 0; i < P.trsm.size(); ++i) {
+    const OpTrsm& t = P.trsm[i];
+    if (t.n > 128) return "trsm: block larger than 128";
+    if (!check(t.L, t.n, t.n, "trsm.L", i) || !check(t.X, t.n, t.c.n, "trsm.X", i)) return msg;
+  }
+  for (size_t i = 0; i < P.potrf.size(); ++i) {
+    const OpPotrf& t = P.potrf[i];
+    if (t.n > 128) return "potrf: block larger than 128";
+    if (!check(t.A, t.n, t.n, "potrf.A", i)) return msg;
+  }
+  for (size_t i = 0; i < P.trunc.size(); ++i) {
+    const OpTrunc& t = P.trunc[i];
+    if (t.kcap > 64) return "trunc: rank capacity above 64";
+    if (!check(t.U, t.m, t.kcap, "trunc.U", i) || !check(t.V, t.n, t.kcap, "trunc.V", i)) return msg;
+    if (t.term0 < 0 || t.term0 + t.nterms > (int64_t)P.terms.size()) return "trunc: term range";
+    for (int q = 0; q < t.nterms; ++q) {
+      const TermD& d = P.terms[t.term0 + q];
+      if (d.roff < 0 || d.coff < 0 || d.roff + d.urows > t.m || d.coff + d.vrows > t.n) return "term: placement";
+      const int64_t k = (d.flags & 1) ? d.urows : (d.flags & 2) ? d.vrows : d.k.n;
+      if (k > 128) return "term: more than 128 columns";
+      if (!(d.flags & 1) && !check(d.U, d.urows, k, "term.U", t.term0 + q)) return msg;
+      if (!(d.flags & 2) && !check(d.V, d.vrows, k, "term.V", t.term0 + q)) return msg;
+    }
+  }
+  return std::string();
+}
+
+}  // namespace hlc

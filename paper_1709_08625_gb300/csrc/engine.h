@@ -1,0 +1,42 @@
+// engine.h -- host tree, layout and planner interfaces.
+#pragma once
+
+#include "hlc_internal.h"
+
+namespace hlc {
+
+struct HTree {
+  int64_t n = 0;
+  int leaf = 64;
+  double eta = 2.0;
+  double eps = 1e-6;
+  int kmax = 64;
+  int depth = 0;
+  std::vector<double> px, py;   // points in tree order
+  std::vector<int32_t> perm;    // tree position -> caller index
+  std::vector<Cluster> cl;      // breadth-first, root = 0
+  std::vector<Block> blk;       // block-cluster tree, root = 0 (diagonal)
+  std::vector<int32_t> leaves;  // leaf blocks, depth-first
+  int64_t arena_doubles = 0;
+  int32_t nslots = 0;
+  int64_t max_dense_dim = 0;
+  std::vector<DenseAsm> dense_asm;
+  std::vector<LrAsm> lr_asm;
+};
+
+// Morton order + breadth-first geometric bisection (host reference build).
+void tree_from_points(HTree& T, const double* x, const double* y, int64_t n, int leaf, double eta);
+bool is_admissible(const HTree& T, int r, int s);
+// Block-cluster tree over the lower triangle, leaves depth-first.
+void block_tree(HTree& T);
+// Arena offsets, rank capacities and rank slots of the leaves.
+void layout(HTree& T, int kmax);
+
+void plan_cholesky(HTree& T, Plan& P);
+void plan_solve(HTree& T, Plan& P, int trans, int64_t voff, int64_t ncols);
+void plan_matvec(HTree& T, Plan& P, int64_t xoff, int64_t yoff, int64_t ncols);
+void plan_recompress(HTree& T, Plan& P);
+// Bounds check of every view against the buffer sizes (in doubles).
+std::string validate_plan(const Plan& P, const int64_t* bufsize);
+
+}  // namespace hlc

@@ -1,0 +1,174 @@
+// hlc_internal.h -- structures shared by the host planner and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/hlc.h"
+
+namespace hlc {
+
+// ---------------------------------------------------------------------------
+// Device-visible descriptors.
+// ---------------------------------------------------------------------------
+
+// Buffers an op view can point into.
+enum Buf : int32_t {
+  BUF_L = 0,     // arena of the matrix being factored / solved with
+  BUF_TMP = 1,   // zero-initialised temporaries of a plan
+  BUF_VEC = 2,   // vectors of the solves (n x c, tree order)
+  BUF_C = 3,     // arena of C~ (matvec, assembly)
+  NBUF = 4
+};
+
+// A strided matrix view: element (i, j) at base[buf] + off + i*rs + j*cs.
+struct Mv {
+  int64_t off;
+  int64_t rs, cs;
+  int32_t buf;
+  int32_t pad;
+};
+
+// A dimension that is either static or the runtime rank of a block
+// (ranks[slot]); the static value is the capacity.
+struct Dim {
+  int32_t n;
+  int32_t slot;
+};
+
+// Y (m x c) = beta * Y + alpha * A (m x k) * B (k x c), beta in {0, 1};
+// B.buf < 0 marks B as the identity (Y = beta Y + alpha A, k = c).
+struct OpGemm {
+  Mv Y, A, B;
+  Dim m, k, c;
+  int32_t beta;
+  int32_t pad;
+  double alpha;
+};
+
+// X (n x c) := L^-1 X (trans = 0) or L^-T X (trans = 1); L dense lower n x n.
+struct OpTrsm {
+  Mv L, X;
+  int32_t n, trans;
+  Dim c;
+};
+
+// In-place lower Cholesky of a dense n x n block.
+struct OpPotrf {
+  Mv A;
+  int32_t n;
+  int32_t row0;  // global row of the block (for the error report)
+};
+
+// One low-rank term of a truncated sum: alpha * U V^T placed at row offset
+// roff / column offset coff of the target.  flags bit 0: U is the identity of
+// size urows (k = urows); bit 1: V is the identity of size vrows.
+struct TermD {
+  Mv U, V;
+  int32_t urows, vrows;
+  int32_t roff, coff;
+  Dim k;
+  int32_t flags;
+  int32_t pad;
+  double alpha;
+};
+
+// Target := trunc(target + sum of terms[term0 .. term0 + nterms)) at block
+// accuracy eps; target U (m x kcap), V (n x kcap), rank in ranks[slot].
+// keep = 0 ignores the target's current content (assembly).
+struct OpTrunc {
+  Mv U, V;
+  int32_t m, n;
+  int32_t kcap, slot;
+  int32_t nterms, keep;
+  int64_t term0;
+  double eps;
+};
+
+// Base pointers handed to every op kernel.
+struct Bases {
+  double* buf[NBUF];
+  int* ranks;      // rank slots of the matrix in BUF_L
+  int* status;     // [0] error code, [1] detail (first error wins)
+  double* scratch; // per-CTA scratch of the truncation kernel
+};
+
+enum OpType : int32_t { OP_POTRF = 0, OP_TRSM = 1, OP_GEMM = 2, OP_TRUNC = 3, NOPTYPES = 4 };
+
+// Device error codes recorded in status[0].
+enum DevErr : int32_t { DEV_OK = 0, DEV_NOT_SPD = 1, DEV_RANK = 2, DEV_BAD = 3 };
+
+// ---------------------------------------------------------------------------
+// Host-side tree.
+// ---------------------------------------------------------------------------
+enum BlkType : int32_t { BT_DENSE = 0, BT_LR = 1, BT_SUB = 2 };
+
+struct Cluster {
+  int64_t lo, hi;
+  double bmin[2], bmax[2];
+  int32_t child[2];
+  int32_t level;
+  bool leaf() const { return child[0] < 0; }
+  int64_t size() const { return hi - lo; }
+};
+
+struct Block {
+  int32_t r, s;
+  int32_t type;
+  int32_t diag;
+  int32_t ch[4];     // off-diagonal: ch[2i+j] = (r_i, s_j); diagonal: 0,2,3
+  int64_t m, n;
+  int64_t offD;      // dense: m x n column-major (ld = m)
+  int64_t offU, offV;// low-rank: U m x kcap (ld m), V n x kcap (ld n)
+  int32_t kcap;
+  int32_t slot;      // rank slot (low-rank) or -1
+  int32_t leaf_index;// position in the leaf list, -1 for SUB
+};
+
+// Assembly descriptors (device).
+struct DenseAsm {
+  int64_t off;   // arena offset
+  int64_t r0, c0;
+  int32_t m, n;
+};
+struct LrAsm {
+  int64_t offU, offV;
+  int64_t r0, c0;
+  int32_t m, n;
+  int32_t kcap, slot;
+};
+
+// A dependency-ordered op program ("plan"): ops grouped into waves; within a
+// wave ops are independent and run as one launch per op type.
+struct Launch {
+  int32_t type;
+  int32_t wave;
+  int64_t first, count;  // range in the per-type device arrays
+};
+
+struct Plan {
+  std::vector<OpGemm> gemm;
+  std::vector<OpTrsm> trsm;
+  std::vector<OpPotrf> potrf;
+  std::vector<OpTrunc> trunc;
+  std::vector<TermD> terms;
+  std::vector<Launch> launches;
+  int64_t tmp_doubles = 0;
+  int32_t nwaves = 0;
+  int64_t max_trunc_per_wave = 0;
+  bool checked = false;
+  // device copies
+  OpGemm* d_gemm = nullptr;
+  OpTrsm* d_trsm = nullptr;
+  OpPotrf* d_potrf = nullptr;
+  OpTrunc* d_trunc = nullptr;
+  TermD* d_terms = nullptr;
+  int64_t nops() const {
+    return (int64_t)gemm.size() + trsm.size() + potrf.size() + trunc.size();
+  }
+};
+
+}  // namespace hlc

@@ -1,0 +1,29 @@
+// kernels.h -- launchers of the device kernels (kernels.cu).
+#pragma once
+
+#include "hlc_internal.h"
+#include "matern.cuh"
+
+namespace hlc {
+
+size_t trunc_smem_bytes();
+int64_t trunc_scratch_doubles();
+int max_trunc_ctas();
+int configure_kernels(int max_dense);
+
+void launch_dense_asm(const DenseAsm* d, int64_t count, double* arena, const double* px, const double* py,
+                      const MaternDev& mp, cudaStream_t st);
+void launch_aca(const LrAsm* d, int64_t count, double* arena, const double* px, const double* py,
+                const MaternDev& mp, double eps, int* ranks, cudaStream_t st);
+void launch_ops(int type, const void* ops, int64_t count, const TermD* terms, const Bases& B, int max_dense,
+                cudaStream_t st);
+void launch_gather(const double* src, const int32_t* perm, double* dst, int64_t n, cudaStream_t st);
+void launch_scatter(const double* src, const int32_t* perm, double* dst, int64_t n, cudaStream_t st);
+void launch_points(const double* xy, const int32_t* perm, double* px, double* py, int64_t n, cudaStream_t st);
+void launch_axpby(double a, const double* x, double b, double* y, int64_t n, cudaStream_t st);
+void launch_sub(const double* x, const double* y, double* z, int64_t n, cudaStream_t st);
+void launch_dot(const double* x, const double* y, int64_t n, double* part, double* out, cudaStream_t st);
+void launch_logdet(const int64_t* offs, const int32_t* dims, int64_t count, const double* arena, double* part,
+                   double* out, cudaStream_t st);
+
+}  // namespace hlc

@@ -1,0 +1,174 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1709_08625_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hlc():
+    from paper_1709_08625_gb300 import build
+
+    build.build()
+    from paper_1709_08625_gb300 import hlc as h
+
+    return h
+
+
+@pytest.fixture(scope="module")
+def ctx(hlc):
+    c = hlc.Context(0)
+    yield c
+    c.close()
+
+
+# --------------------------------------------------------------------------
+# tree and block tree: bit-exact structure
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n,leaf,eta", [(2000, 32, 2.0), (3001, 64, 2.0), (777, 16, 0.7), (40, 64, 2.0)])
+def test_tree_structure_matches_oracle(ctx, n, leaf, eta):
+    xy = inputs.points(n, 500 + n)
+    t = ctx.build_tree(xy, leaf=leaf, eta=eta)
+    H = oracle.HOracle(xy, leaf=leaf, eta=eta)
+    np.testing.assert_array_equal(t.perm(), H.perm())
+    np.testing.assert_array_equal(t.leaf_blocks(), H.leaf_blocks())
+
+
+# --------------------------------------------------------------------------
+# assembly: dense leaves exactly (Matern eq. 3), low-rank leaves to eps
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("nu", [0.5, 1.5, 0.325, 1.0, 2.2])
+def test_assembly_entries(ctx, hlc, nu):
+    n, ell, eps = 1500, 0.08, 1e-8
+    xy = inputs.points(n, 600)
+    t = ctx.build_tree(xy, leaf=32, eps=eps)
+    C = t.assemble(hlc.theta(1.3, ell, nu, 1e-4))
+    Ct = C.expand()
+    Cd = oracle.dense_cov(xy, 1.3, ell, nu, 1e-4)
+    blocks = t.leaf_blocks()
+    perm = t.perm()
+    for r0, r1, c0, c1, ty in blocks:
+        ri, ci = perm[r0:r1], perm[c0:c1]
+        got = Ct[np.ix_(ri, ci)]
+        ref = Cd[np.ix_(ri, ci)]
+        if ty == 0:
+            np.testing.assert_allclose(got, ref, rtol=1e-13, atol=1e-15)
+        else:
+            assert np.linalg.norm(got - ref) <= 20 * eps * np.linalg.norm(ref) + 1e-300
+
+
+def test_assembly_vs_h_oracle_ranks(ctx, hlc):
+    n = 2000
+    xy = inputs.points(n, 601)
+    t = ctx.build_tree(xy, leaf=32, eps=1e-7)
+    C = t.assemble(hlc.theta(1.0, 0.1, 0.5, 1e-4))
+    H = oracle.HOracle(xy, leaf=32)
+    H.assemble(1.0, 0.1, 0.5, 1e-4, 1e-7)
+    rg, ro = C.ranks(), H.ranks(0)
+    assert np.all((rg < 0) == (ro < 0))
+    assert np.max(np.abs(rg - ro)) <= 1
+    np.testing.assert_allclose(C.expand(), H.expand(0), atol=1e-9)
+
+
+def test_matvec(ctx, hlc):
+    n = 3000
+    xy = inputs.points(n, 602)
+    t = ctx.build_tree(xy, leaf=32, eps=1e-8)
+    C = t.assemble(hlc.theta(1.0, 0.05, 1.5, 1e-4))
+    x = inputs.normal(n, 603)
+    y = C.matvec(x)
+    ref = C.expand() @ x
+    np.testing.assert_allclose(y, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+# --------------------------------------------------------------------------
+# H-Cholesky and the likelihood
+# --------------------------------------------------------------------------
+def test_cholesky_reproduces_matrix(ctx, hlc):
+    n, eps = 2000, 1e-7
+    xy = inputs.points(n, 604)
+    t = ctx.build_tree(xy, leaf=32, eps=eps)
+    C = t.assemble(hlc.theta(1.0, 0.1, 0.5, 1e-4))
+    L = t.cholesky(C)
+    Ct, Lt = C.expand(), L.expand()
+    err = np.linalg.norm(Ct - Lt @ Lt.T, 2) / np.linalg.norm(Ct, 2)
+    assert err <= 20 * eps, err
+    H = oracle.HOracle(xy, leaf=32)
+    H.assemble(1.0, 0.1, 0.5, 1e-4, eps)
+    H.cholesky(eps)
+    Lo = H.expand(1)
+    assert np.linalg.norm(Lt - Lo, 2) / np.linalg.norm(Lo, 2) <= 50 * eps
+
+
+def test_loglik_n2000_vs_dense_oracle(ctx, hlc):
+    name = "n2000_nu0.5_eps1e-7"
+    w = inputs.WORKLOADS[name]
+    xy = inputs.workload_points(name)
+    xi = inputs.workload_normal(name)
+    th = (w["sigma2"], w["ell"], w["nu"], w["nugget"])
+    z = oracle.dense_chol_apply(xy, xi, *th)
+    Ld, ldd, qd = oracle.dense_loglik(xy, z, *th)
+    t = ctx.build_tree(xy, leaf=w["leaf"], eta=w["eta"], eps=w["eps"])
+    r = t.loglik(hlc.theta(*th), z)
+    assert abs(r["loglik"] - Ld) / w["n"] <= 1e-6
+    assert abs(r["logdet"] - ldd) / w["n"] <= 1e-6
+    assert r["rel_residual"] <= 1e-12
+    # with z = L xi the exact quadratic form is |xi|^2
+    assert abs(r["quad"] - xi @ xi) / w["n"] <= 1e-6
+    ho = oracle.h_loglik(xy, z, *th, w["eps"], leaf=w["leaf"], eta=w["eta"])
+    assert abs(r["loglik"] - ho["loglik"]) / w["n"] <= 1e-8
+    assert abs(r["logdet"] - ho["logdet"]) / w["n"] <= 1e-8
+
+
+@pytest.mark.parametrize("n,leaf,nu,eps", [(3001, 64, 1.5, 1e-6), (1, 64, 0.5, 1e-6), (2, 64, 0.5, 1e-6),
+                                           (64, 64, 0.325, 1e-6), (65, 64, 0.5, 1e-6), (5000, 32, 0.325, 1e-6)])
+def test_loglik_vs_h_oracle(ctx, hlc, n, leaf, nu, eps):
+    # Any data vector: the GPU H-path follows the oracle's H-arithmetic.
+    xy = inputs.points(n, 700 + n)
+    z = inputs.normal(n, 800 + n)
+    th = (1.0, 0.05, nu, 1e-4)
+    t = ctx.build_tree(xy, leaf=leaf, eps=eps)
+    r = t.loglik(hlc.theta(*th), z)
+    ho = oracle.h_loglik(xy, z, *th, eps, leaf=leaf)
+    assert abs(r["loglik"] - ho["loglik"]) / n <= 1e-7
+    assert abs(r["logdet"] - ho["logdet"]) / n <= 1e-8
+
+
+@pytest.mark.parametrize("n,leaf,nu,eps", [(3001, 64, 1.5, 1e-6), (5000, 32, 0.325, 1e-6), (1, 64, 0.5, 1e-6),
+                                           (65, 64, 0.5, 1e-7)])
+def test_loglik_vs_dense_model_data(ctx, hlc, n, leaf, nu, eps):
+    # Data drawn from the model (z = L xi, Sec. 5.1): the H-likelihood stays
+    # within 1e-6 per location of the exact eq. (1).
+    xy = inputs.points(n, 700 + n)
+    th = (1.0, 0.05, nu, 1e-4)
+    z = oracle.dense_chol_apply(xy, inputs.normal(n, 800 + n), *th)
+    t = ctx.build_tree(xy, leaf=leaf, eps=eps)
+    r = t.loglik(hlc.theta(*th), z)
+    Ld = oracle.dense_loglik(xy, z, *th)[0]
+    assert abs(r["loglik"] - Ld) / n <= 1e-6
+
+
+def test_not_spd_is_reported(ctx, hlc):
+    xy = inputs.points(200, 900)
+    xy[7] = xy[3]  # duplicate location, no nugget
+    t = ctx.build_tree(xy, leaf=32, eps=1e-10)
+    with pytest.raises(hlc.HlcError) as e:
+        t.loglik(hlc.theta(1.0, 0.3, 1.5, 0.0), inputs.normal(200, 901))
+    assert e.value.status in (-3, -9)
+
+
+def test_device_pointers_through_torch(ctx, hlc):
+    torch = pytest.importorskip("torch")
+    n = 1000
+    xy = inputs.points(n, 902)
+    z = inputs.normal(n, 903)
+    t1 = ctx.build_tree(xy, leaf=32, eps=1e-8)
+    r1 = t1.loglik(hlc.theta(1.0, 0.1, 0.5, 1e-4), z)
+    t2 = ctx.build_tree(torch.tensor(xy, device="cuda"), leaf=32, eps=1e-8)
+    r2 = t2.loglik(hlc.theta(1.0, 0.1, 0.5, 1e-4), torch.tensor(z, device="cuda"))
+    assert r1["loglik"] == r2["loglik"]
