@@ -243,7 +243,7 @@ class HOracle:
             raise RuntimeError("not assembled / factored")
         return out
 
-    def loglik(self, z, tol=1e-12, maxit=20):
+    def loglik(self, z, tol=1e-12, maxit=100):
         z = np.ascontiguousarray(z, dtype=np.float64)
         out = np.zeros(6)
         if lib().orc_h_loglik(self.h, _d(z), float(tol), int(maxit), _d(out)) != 0:
@@ -264,8 +264,8 @@ class HOracle:
         return Uk, Vk
 
 
-def h_loglik(xy, z, sigma2, ell, nu, nugget, eps, leaf=32, eta=2.0, tol=1e-12, maxit=20):
-    """One oracle evaluation: tree, assembly, H-Cholesky, eq. (2) + refinement."""
+def h_loglik(xy, z, sigma2, ell, nu, nugget, eps, leaf=32, eta=2.0, tol=1e-12, maxit=100):
+    """One oracle evaluation: tree, assembly, H-Cholesky, eq. (2) + preconditioned CG."""
     H = HOracle(xy, leaf=leaf, eta=eta)
     H.assemble(sigma2, ell, nu, nugget, eps)
     H.cholesky(eps)

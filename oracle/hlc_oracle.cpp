@@ -21,9 +21,8 @@
 //         QR+SVD recompression (Remark A.1) to block accuracy eps (Sec. 2.2),
 //       - recursive H-Cholesky built from the H-arithmetic of Table 1
 //         (truncated add and multiply-add), eq. (2) for the likelihood,
-//       - forward/backward H-solves, the H-matvec, and the factor-
-//         preconditioned FP64 iterative refinement standing in for the
-//         preconditioned CG of App. B.
+//       - forward/backward H-solves, the H-matvec, and the conjugate
+//         gradients on C~ preconditioned with the factor (App. B listing).
 //
 // Parity pins live in tests/test_oracle_pins.py (closed forms, Bessel
 // identities and library values, brute-force determinants, invariants).
@@ -1376,10 +1375,11 @@ int orc_h_expand(void* h, int which, double* out) {
   return 0;
 }
 
-// Likelihood from the factor, eq. (2), plus the refined quadratic form.
-// out = {loglik, logdet, quad, quad_factor, refine_iters, rel_residual}
-// loglik uses quad = z^T x with x refined against C~ until
-// |z - C~ x| <= tol |z| or maxit corrections.
+// Likelihood from the factor, eq. (2), plus the quadratic form z^T C~^-1 z
+// from conjugate gradients on C~ preconditioned with (L~ L~^T)^-1, the
+// solver of the App. B listing (CG with the inverse factor as
+// preconditioner), run to |z - C~ x| <= tol |z| or maxit iterations.
+// out = {loglik, logdet, quad, quad_factor, iterations, rel_residual}
 int orc_h_loglik(void* h, const double* z, double tol, int maxit, double* out) {
   HTree* T = static_cast<HTree*>(h);
   if (!T->factored) return -3;
@@ -1394,36 +1394,63 @@ int orc_h_loglik(void* h, const double* z, double tol, int maxit, double* out) {
     if (bl.diag)
       for (long i = 0; i < bl.D.m; ++i) logdet += 2.0 * std::log(bl.D(i, i));
   }
+  auto dot = [n](const std::vector<double>& a, const std::vector<double>& b) {
+    double s = 0.0;
+    for (long i = 0; i < n; ++i) s += a[i] * b[i];
+    return s;
+  };
+  auto precond = [&](std::vector<double>& v) {  // v := (L L^T)^-1 v
+    trsv(HL, 0, View{v.data(), n, 1, n});
+    trsv_t(HL, 0, View{v.data(), n, 1, n});
+  };
+  auto apply_C = [&](const std::vector<double>& x, std::vector<double>& y) {
+    std::fill(y.begin(), y.end(), 0.0);
+    symv(HC, 0, View{const_cast<double*>(x.data()), n, 1, n}, View{y.data(), n, 1, n});
+  };
   std::vector<double> zt(n);
   for (long i = 0; i < n; ++i) zt[i] = z[T->perm[i]];
+  // eq. (2): v = L^-1 z, quad_factor = v^T v
   std::vector<double> v = zt;
   trsv(HL, 0, View{v.data(), n, 1, n});
-  double qf = 0.0;
-  for (double t : v) qf += t * t;
-  std::vector<double> xs = v;
-  trsv_t(HL, 0, View{xs.data(), n, 1, n});
-  double zn = 0.0;
-  for (double t : zt) zn += t * t;
-  zn = std::sqrt(zn);
+  const double qf = dot(v, v);
+  // PCG with x0 = (L L^T)^-1 z
+  std::vector<double> x = v;
+  trsv_t(HL, 0, View{x.data(), n, 1, n});
+  std::vector<double> r(n), q(n), p(n), w(n);
+  apply_C(x, q);
+  for (long i = 0; i < n; ++i) r[i] = zt[i] - q[i];
+  const double zn = std::sqrt(dot(zt, zt));
+  double rel = zn > 0.0 ? std::sqrt(dot(r, r)) / zn : 0.0;
   int it = 0;
-  double rel = 0.0;
-  for (;;) {
-    std::vector<double> r(n, 0.0);
-    symv(HC, 0, View{xs.data(), n, 1, n}, View{r.data(), n, 1, n});
-    double rn = 0.0;
-    for (long i = 0; i < n; ++i) {
-      r[i] = zt[i] - r[i];
-      rn += r[i] * r[i];
+  if (rel > tol) {
+    w = r;
+    precond(w);
+    p = w;
+    double rw = dot(r, w);
+    while (it < maxit) {
+      apply_C(p, q);
+      const double alpha = rw / dot(p, q);
+      for (long i = 0; i < n; ++i) {
+        x[i] += alpha * p[i];
+        r[i] -= alpha * q[i];
+      }
+      ++it;
+      rel = zn > 0.0 ? std::sqrt(dot(r, r)) / zn : 0.0;
+      if (rel <= tol) break;
+      w = r;
+      precond(w);
+      const double rw1 = dot(r, w);
+      const double beta = rw1 / rw;
+      rw = rw1;
+      for (long i = 0; i < n; ++i) p[i] = w[i] + beta * p[i];
     }
-    rel = zn > 0.0 ? std::sqrt(rn) / zn : 0.0;
-    if (rel <= tol || it >= maxit) break;
-    trsv(HL, 0, View{r.data(), n, 1, n});
-    trsv_t(HL, 0, View{r.data(), n, 1, n});
-    for (long i = 0; i < n; ++i) xs[i] += r[i];
-    ++it;
   }
-  double quad = 0.0;
-  for (long i = 0; i < n; ++i) quad += zt[i] * xs[i];
+  // true residual at exit
+  apply_C(x, q);
+  double rn = 0.0;
+  for (long i = 0; i < n; ++i) rn += (zt[i] - q[i]) * (zt[i] - q[i]);
+  rel = zn > 0.0 ? std::sqrt(rn) / zn : 0.0;
+  const double quad = dot(zt, x);
   out[0] = -0.5 * n * std::log(2.0 * M_PI) - 0.5 * logdet - 0.5 * quad;
   out[1] = logdet;
   out[2] = quad;
