@@ -600,11 +600,19 @@ void aca(const HTree& T, long r0, long m, long c0, long n, double eps, long kmax
 // ---------------------------------------------------------------------------
 // H-arithmetic (Table 1) for the recursive H-Cholesky of eq. (2).
 // ---------------------------------------------------------------------------
+// A low-rank term of a product, placed at (roff, coff) inside the target.
+struct Term {
+  Mat U, V;
+  long roff, coff;
+};
+
 struct HCtx {
   HTree* T;
   std::vector<Block>* B;
   double eps;
   long err = 0;
+  // accumulated updates of low-rank blocks (see add_lr / flush)
+  std::vector<std::vector<Term>>* pending = nullptr;
   const Cluster& cl(int c) const { return T->cl[c]; }
   Block& b(int i) { return (*B)[i]; }
   long rows(int i) { return cl(b(i).r).size(); }
@@ -615,7 +623,10 @@ struct HCtx {
 bool big(HCtx& H, int c) { return H.rows(c) * H.cols(c) >= 64L * 1024; }
 
 // Y += alpha * A X ; A off-diagonal (any type), X |s| x c, Y |r| x c.
+void flush(HCtx& H, int b);
+
 void hmul(HCtx& H, int a, const View& X, const View& Y, double alpha) {
+  flush(H, a);
   Block& A = H.b(a);
   const long c = X.n;
   if (A.type == DENSE) {
@@ -653,6 +664,7 @@ void hmul(HCtx& H, int a, const View& X, const View& Y, double alpha) {
 
 // Y += alpha * A^T X ; A off-diagonal, X |r| x c, Y |s| x c.
 void hmul_t(HCtx& H, int a, const View& X, const View& Y, double alpha) {
+  flush(H, a);
   Block& A = H.b(a);
   const long c = X.n;
   if (A.type == DENSE) {
@@ -732,14 +744,32 @@ void trsv_t(HCtx& H, int l, const View& X) {
   trsv_t(H, Ld.ch[0], X0);
 }
 
-// A low-rank term of a product, placed at (roff, coff) inside the target.
-struct Term {
-  Mat U, V;
-  long roff, coff;
-};
-
 void add_lr(HCtx& H, int c, const View& U, const View& V);
 void add_dense(HCtx& H, int c, const View& P);
+
+void add_terms(HCtx& H, int c, std::vector<Term>& terms);
+
+// Accumulated updates: terms added to a low-rank block during the
+// factorisation wait in a list and are truncated together (add_terms, in
+// batches) right before the block is next read or rewritten, and at the end.
+void queue_terms(HCtx& H, int c, std::vector<Term>& terms) {
+  if (!H.pending) {
+    add_terms(H, c, terms);
+    return;
+  }
+  std::vector<Term>& q = (*H.pending)[c];
+#pragma omp critical(hlc_pending)
+  for (Term& t : terms) q.push_back(std::move(t));
+}
+
+void flush(HCtx& H, int b) {
+  if (!H.pending || H.b(b).type != LOWRANK) return;
+  std::vector<Term>& q = (*H.pending)[b];
+  if (q.empty()) return;
+  std::vector<Term> terms;
+  terms.swap(q);
+  add_terms(H, b, terms);
+}
 
 // Truncated sum C := trunc(C + sum_t U_t V_t^T) for a low-rank target
 // (the truncated addition of Table 1).  Terms are added in batches of at most
@@ -754,7 +784,8 @@ void add_terms(HCtx& H, int c, std::vector<Term>& terms) {
   while (t0 < terms.size()) {
     size_t t1 = t0;
     long kb = 0;
-    while (t1 < terms.size() && (kb == 0 || kb + terms[t1].U.n <= kTruncBatch)) kb += terms[t1++].U.n;
+    while (t1 < terms.size() && (kb == 0 || kb + terms[t1].U.n <= kTruncBatch) && t1 - t0 < 64)
+      kb += terms[t1++].U.n;
     const long K = C.U.n + kb;
     Mat U(m, K), V(n, K);
     long col = 0;
@@ -795,7 +826,7 @@ void add_lr(HCtx& H, int c, const View& U, const View& V) {
       for (long i = 0; i < V.m; ++i) ts[0].V(i, l) = V.at(i, l);
     }
     ts[0].roff = ts[0].coff = 0;
-    add_terms(H, c, ts);
+    queue_terms(H, c, ts);
   } else {
     const long r0 = H.cl(C.r).lo, s0 = H.cl(C.s).lo;
     const bool spawn = big(H, c);
@@ -837,7 +868,7 @@ void add_dense(HCtx& H, int c, const View& P) {
       for (long j = 0; j < P.n; ++j)
         for (long i = 0; i < P.m; ++i) t.U(i, j) = P.at(i, j);
     }
-    add_terms(H, c, ts);
+    queue_terms(H, c, ts);
   } else {
     const long r0 = H.cl(C.r).lo, s0 = H.cl(C.s).lo;
     for (int q = 0; q < 4; ++q) {
@@ -862,6 +893,8 @@ Mat transpose(const Mat& A) {
 // The exact product A B^T (A = (r, s), B = (r', s)) as a list of low-rank
 // terms placed inside the |r| x |r'| target.
 void prod_terms(HCtx& H, int a, int bb, long roff, long coff, std::vector<Term>& out) {
+  flush(H, a);
+  flush(H, bb);
   Block& A = H.b(a);
   Block& B = H.b(bb);
   const long ra = H.rows(a), rb = H.rows(bb);
@@ -923,6 +956,8 @@ void prod_terms(HCtx& H, int a, int bb, long roff, long coff, std::vector<Term>&
 
 // C += alpha * A B^T with truncation; A = (r, s), B = (r', s), C = (r, r').
 void mul_add(HCtx& H, int c, int a, int bb, double alpha) {
+  flush(H, a);
+  flush(H, bb);
   const int ta = H.b(a).type, tb = H.b(bb).type, tc = H.b(c).type;
   const long ra = H.rows(a), rb = H.rows(bb);
   if (ta == LOWRANK) {
@@ -984,7 +1019,7 @@ void mul_add(HCtx& H, int c, int a, int bb, double alpha) {
       for (Term& t : terms)
         for (double& v : t.U.a) v *= alpha;
     if (tc == LOWRANK) {
-      add_terms(H, c, terms);
+      queue_terms(H, c, terms);
     } else {
       Mat P(ra, rb);
       for (const Term& t : terms)
@@ -1000,6 +1035,7 @@ void mul_add(HCtx& H, int c, int a, int bb, double alpha) {
 
 // B := B L^-T for an off-diagonal block B = (r, s) and factored L = (s, s).
 void trsm(HCtx& H, int l, int bb) {
+  flush(H, bb);
   Block& B = H.b(bb);
   if (B.type == DENSE) {
     Mat Xt = transpose(B.D);
@@ -1297,10 +1333,13 @@ long orc_h_cholesky(void* h, double eps) {
   HTree* T = static_cast<HTree*>(h);
   if (!T->assembled) return -3;
   T->L = T->C;
+  std::vector<std::vector<Term>> pending(T->L.size());
   HCtx H{T, &T->L, eps};
+  H.pending = &pending;
 #pragma omp parallel
 #pragma omp single
   chol(H, 0);
+  for (size_t b = 0; b < T->L.size(); ++b) flush(H, (int)b);
   if (H.err) {
     T->factored = false;
     return -2;
