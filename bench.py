@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Throughput of the H-matrix Gaussian log-likelihood on GB300.
+
+One step = one likelihood evaluation (arXiv:1709.08625, eq. 2) at
+n = 524,288 uniform locations in [0,1]^2 on an existing tree: Matern assembly
+(dense leaves + ACA + recompression), H-Cholesky, log det, forward solve and
+the FP64 preconditioned-CG quadratic form.  theta varies by +-5 % (sigma2,
+ell) from step to step.  The working set (tens of GB of H-matrix storage) is
+far larger than L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU runs (torchrun, one rank per GPU) are replicas: every rank runs its
+own evaluations on its own GPU; value = evaluations of all ranks / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "loglik evals/s at n=512k (mixed vs FP64, |ΔL|/n≤1e-6); serve p50/p99 ms"
+UNIT = "evals/s"
+WORKLOAD = "n524288_nu0.5_eps1e-5"
+SAMPLE_N = 16384  # oracle sample: the first SAMPLE_N locations of the workload
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--no-fp64-check", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--kmax", type=int, default=64)
+    p.add_argument("--sample-n", type=int, default=SAMPLE_N,
+                   help="locations in the oracle's bounded sample of the workload")
+    return p.parse_args()
+
+
+# --------------------------------------------------------------------------
+# distributed plumbing (replicas)
+# --------------------------------------------------------------------------
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0, None
+    import torch
+    import torch.distributed as dist
+
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if backend == "nccl":
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend=backend)
+    return rank, ws, local, dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, v):
+    if dist is None:
+        return v
+    import torch
+
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) >= 9:
+                for nm, v in zip(names, r[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# CPU baseline: the oracle on a bounded sample of the workload
+# --------------------------------------------------------------------------
+def oracle_sample(name, n_sample):
+    import oracle
+    from paper_1709_08625_gb300 import inputs
+
+    w = inputs.WORKLOADS[name]
+    xy = inputs.workload_points(name)[:n_sample]
+    z = inputs.workload_normal(name)[:n_sample]
+    t0 = time.perf_counter()
+    r = oracle.h_loglik(xy, z, w["sigma2"], w["ell"], w["nu"], w["nugget"], w["eps"], leaf=w["leaf"], eta=w["eta"])
+    dt = time.perf_counter() - t0
+    N = w["n"]
+    # scale one sample evaluation to one evaluation of the full workload by
+    # the paper's complexity O(k^2 n log^2 n) (Table 1, technical details)
+    scale = (N * math.log(N) ** 2) / (n_sample * math.log(n_sample) ** 2)
+    return {"value": 1.0 / (dt * scale), "scale": scale, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"one oracle evaluation on the first {n_sample} locations of the {name} workload "
+                      f"({dt:.2f} s), scaled to n={N} by n log^2 n", "sample_seconds": dt,
+            "sample_loglik": r["loglik"]}
+
+
+def run_reference(args, rank, ws, dist):
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    times = []
+    last = None
+    for _ in range(args.warmup):
+        oracle_sample(args.workload, args.sample_n)
+    for _ in range(args.steps):
+        last = oracle_sample(args.workload, args.sample_n)
+        times.append(last["sample_seconds"])
+    # each step: one oracle evaluation of the sample, scaled to the workload
+    v = 1.0 / (statistics.median(times) * last["scale"])
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "sample_n": args.sample_n},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
+                            "sample": last["sample"]},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+def run_ours(args, rank, ws, local, dist):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1709_08625_gb300 import hlc, inputs
+
+    dev = local
+    torch.cuda.set_device(dev)
+    w = inputs.WORKLOADS[args.workload]
+    n = w["n"]
+    xy = inputs.workload_points(args.workload)
+    z_host = inputs.workload_normal(args.workload)
+    prec = hlc.HLC_MIXED if args.precision == "mixed" else hlc.HLC_FP64
+    ctx = hlc.Context(dev)
+    t0 = time.perf_counter()
+    tree = ctx.build_tree(xy, leaf=w["leaf"], eta=w["eta"], eps=w["eps"], precision=prec, kmax=args.kmax)
+    tree_s = time.perf_counter() - t0
+    z_dev = torch.tensor(z_host, device=f"cuda:{dev}")
+    z_pin = torch.tensor(z_host).pin_memory()
+    stream = torch.cuda.ExternalStream(ctx.stream(), device=f"cuda:{dev}")
+
+    def theta(k):
+        j = inputs.theta_jitter(w, k)
+        return hlc.theta(j["sigma2"], j["ell"], w["nu"], w["nugget"])  # nu fixed: same kernel class
+
+    first = time.perf_counter()
+    for k in range(args.warmup):
+        tree.loglik(theta(k), z_dev)
+    warm_s = time.perf_counter() - first
+
+    # ---- timed region: device time on the library stream --------------------
+    ctx.set_profiling(False)
+    ctx.counters(reset=True)
+    clocks = ClockSampler(dev)
+    clocks.start()
+    barrier(dist)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    results = []
+    for k in range(args.steps):
+        results.append(tree.loglik(theta(1000 + k), z_dev))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    clk = clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    cnt = ctx.counters(reset=True)
+    ms_total = max_over_ranks(dist, ms_total)
+    value = ws * args.steps / (ms_total / 1000.0)
+
+    # ---- profiled pass of the same steps: per-kernel launch times ------------
+    ctx.set_profiling(True)
+    torch.cuda.synchronize()
+    pe0 = torch.cuda.Event(enable_timing=True)
+    pe1 = torch.cuda.Event(enable_timing=True)
+    pe0.record(stream)
+    for k in range(args.steps):
+        tree.loglik(theta(1000 + k), z_dev)
+    pe1.record(stream)
+    torch.cuda.synchronize()
+    prof = ctx.counters(reset=True)
+    ctx.set_profiling(False)
+    prof_ms = pe0.elapsed_time(pe1)
+
+    # ---- end to end through the public API with host buffers ---------------
+    t0 = time.perf_counter()
+    e2e_res = None
+    for k in range(args.steps):
+        e2e_res = tree.loglik(theta(1000 + k), z_pin.numpy())
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(dist, time.perf_counter() - t0)
+    e2e_value = ws * args.steps / e2e_s
+    info = tree.info()
+    iters = e2e_res["refine_iters"]
+    # bytes read back per evaluation: scalars of the solve, status words and
+    # the two rank arrays for the storage statistics
+    d2h = 8 * (8 + 3 * iters) + 8 * 3 + 2 * 4 * info["lowrank"]
+
+    out = {}
+    if rank == 0:
+        # dominant op kernel of the profiled pass
+        ops = {k: v for k, v in prof.items() if isinstance(v, dict)}
+        dom = max(ops, key=lambda k: ops[k]["ms"])
+        d = ops[dom]
+        sm_mhz = clk.get("sm_max_mhz") or 2070.0
+        if args.precision == "mixed" and dom in ("gemm", "trunc", "trunc_cluster"):
+            peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+            unit = "TFLOP/s"
+        else:
+            peak = 1.25  # nominal FP64 rate of GB300
+            unit = "TFLOP/s"
+        achieved = d["flops"] / (d["ms"] / 1000.0) / 1e12 if d["ms"] > 0 else 0.0
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+            "data": "synthetic: seeded uniform locations in [0,1]^2, z ~ N(0,1); theta +-5 % per step",
+            "config": {"workload": args.workload, "n": n, "nu": w["nu"], "ell": w["ell"], "sigma2": w["sigma2"],
+                       "nugget": w["nugget"], "eps": w["eps"], "leaf": w["leaf"], "eta": w["eta"],
+                       "precision": args.precision, "kmax": args.kmax,
+                       "l2": "no flush: H-matrix working set of several GB > 129 MB L2",
+                       "parallelism": f"replicas x{ws}", "tree_build_s": tree_s, "warmup_s": warm_s,
+                       "plan_ops": info["plan_ops"], "plan_waves": info["plan_waves"]},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(cnt["launches"]),
+            "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
+                         "frac": achieved / peak if peak else None, "traffic": None,
+                         "peak_note": ("FP32 SIMT: 152 SMs x 128 lanes x 2 flop x max SM clock"
+                                       if unit == "TFLOP/s" and peak > 2 else "nominal FP64 rate"),
+                         "profiled_ms_per_step": prof_ms / args.steps,
+                         "per_kernel": {k: v for k, v in ops.items()}},
+            "clocks": clk,
+            "result": {k: results[-1][k] for k in ("loglik", "logdet", "quad", "refine_iters", "rel_residual",
+                                                   "max_rank_C", "max_rank_L", "bytes_C", "bytes_L",
+                                                   "ms_assemble", "ms_factor", "ms_solve")},
+        }
+    # ---- FP64 comparison at the same theta ---------------------------------
+    if rank == 0 and not args.no_fp64_check and args.precision == "mixed":
+        del tree
+        t64 = ctx.build_tree(xy, leaf=w["leaf"], eta=w["eta"], eps=w["eps"], precision=hlc.HLC_FP64,
+                             kmax=args.kmax)
+        t0 = time.perf_counter()
+        r64 = t64.loglik(theta(1000 + args.steps - 1), z_dev)
+        s64 = time.perf_counter() - t0
+        rm = results[-1]
+        out["fp64"] = {"value": 1.0 / s64, "unit": UNIT, "steps": 1, "ms_per_step": 1000 * s64,
+                       "note": "first evaluation on a fresh FP64 tree (plans built before timing)",
+                       "loglik": r64["loglik"], "ms_factor": r64["ms_factor"]}
+        out["parity"] = {"dL_per_n_mixed_vs_fp64": abs(rm["loglik"] - r64["loglik"]) / n,
+                         "dlogdet_per_n": abs(rm["logdet"] - r64["logdet"]) / n,
+                         "dquad_per_n": abs(rm["quad"] - r64["quad"]) / n, "bar": 1e-6,
+                         "speedup_mixed_vs_fp64": value / ws / out["fp64"]["value"]}
+        del t64
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            import oracle
+
+            oracle.build()
+            out["cpu_baseline"] = {k: v for k, v in oracle_sample(args.workload, args.sample_n).items()
+                                   if k not in ("sample_seconds", "sample_loglik", "scale")}
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    return 0
+
+
+def main():
+    args = parse()
+    rank, ws, local, dist = dist_setup(args)
+    try:
+        if args.impl == "reference":
+            return run_reference(args, rank, ws, dist)
+        return run_ours(args, rank, ws, local, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

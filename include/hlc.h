@@ -77,9 +77,9 @@ typedef struct {
   double eta;         /* standard admissibility parameter (App. A), > 0 */
   double eps;         /* block accuracy of C~ and of the H-arithmetic (Sec. 2.2) */
   int precision;      /* HLC_FP64 or HLC_MIXED */
-  double refine_tol;  /* stop refinement when |z - C~ x| <= refine_tol |z| */
-  int refine_maxit;   /* at most this many refinement corrections */
-  int kmax;           /* rank capacity of a low-rank block, 1..64 */
+  double refine_tol;  /* stop the solve when |z - C~ x| <= refine_tol |z| */
+  int refine_maxit;   /* at most this many preconditioned CG iterations */
+  int kmax;           /* rank capacity of a low-rank block, 1..128 */
 } hlc_params;
 
 typedef struct {
@@ -87,16 +87,17 @@ typedef struct {
   double logdet;       /* 2 sum log L~_ii */
   double quad;         /* z^T x, x refined against C~ */
   double quad_factor;  /* v^T v with L~ v = z (eq. 2 as printed) */
-  int refine_iters;    /* refinement corrections applied */
+  int refine_iters;    /* preconditioned CG iterations */
   double rel_residual; /* |z - C~ x| / |z| at exit */
   size_t bytes_C;      /* storage of C~ (actual ranks) */
   size_t bytes_L;      /* storage of L~ (actual ranks) */
   int max_rank_C, max_rank_L;
   double ms_assemble, ms_factor, ms_solve; /* device time per phase */
+  double ms_total;     /* served requests: submit-to-completion wall time */
 } hlc_result;
 
 /* Defaults: leaf 64, eta 2, eps 1e-6, HLC_FP64, refine_tol 1e-12,
- * refine_maxit 30, kmax 64. */
+ * refine_maxit 100, kmax 64. */
 void hlc_default_params(hlc_params* p);
 
 /* Description of a status code (static string, never NULL). */
@@ -154,22 +155,45 @@ void hlc_hmat_free(hlc_hmat* M);
 
 /*
  * One likelihood evaluation on an existing tree: assemble C~(theta), factor,
- * log det, forward solve (eq. 2), FP64 refinement of C~^-1 z, assemble L.
+ * log det, forward solve (eq. 2), C~^-1 z by conjugate gradients preconditioned
+ * with the factor (App. B), in FP64; assemble L.
  * z: n values in caller order (host or device).  Uses the tree's cached
  * workspace; no device allocation after the first call on a tree.
  */
 int hlc_loglik(hlc_ctx* ctx, hlc_tree* t, const hlc_theta* th, const double* z,
                hlc_result* out);
 
+/* ---- measurement ---------------------------------------------------------- */
+/* The context's CUDA stream (cudaStream_t) in *stream, for timing with events
+ * recorded on the stream the kernels run on. */
+int hlc_ctx_stream(hlc_ctx* ctx, void** stream);
+/* on = 1: count kernel launches, time every launch of the op kernels with
+ * CUDA events and accumulate their algorithmic flops (small overhead);
+ * on = 0: counting only. */
+int hlc_ctx_set_profiling(hlc_ctx* ctx, int on);
+/* Counters since the last reset (reset = 1 clears them after reading):
+ * out[0] kernel launches of the library,
+ * out[1 + 3*t .. 3 + 3*t] for op type t in {0 potrf, 1 trsm, 2 gemm,
+ *   3 truncation (one CTA), 4 truncation (cluster)}: launches, device ms
+ *   (profiling on), algorithmic flops.  17 doubles. */
+int hlc_ctx_counters(hlc_ctx* ctx, int reset, double* out);
+
 /* ---- serving: continuous batching of likelihood requests ------------------ */
-/* Start the request loop with a device-memory budget and a slot limit. */
+/* Start the request loop with a device-memory budget and a slot limit.
+ * max_slots slot workers (each its own context, stream and workspaces) admit
+ * queued requests in arrival order as soon as a slot is free and the
+ * request's estimated device footprint fits in what the budget has left;
+ * admitted requests run concurrently on the device. */
 int hlc_serve_start(hlc_ctx* ctx, size_t hbm_budget_bytes, int max_slots);
-/* Queue one request (copies xy and z); returns its id in *req_id. */
+/* Queue one request (copies host arrays xy (n x 2 row-major) and z; p may be
+ * NULL for the defaults); returns its id in *req_id. */
 int hlc_serve_submit(hlc_ctx* ctx, const double* xy, const double* z, int64_t n,
                      const hlc_theta* th, const hlc_params* p, uint64_t* req_id);
-/* HLC_PENDING until done; then the request's status with *out filled. */
+/* HLC_PENDING until done; then the request's status with *out filled
+ * (ms_total = submit-to-completion wall time).  A finished request is
+ * forgotten once polled. */
 int hlc_serve_poll(hlc_ctx* ctx, uint64_t req_id, hlc_result* out);
-/* Drain and stop the loop. */
+/* Finish every queued request, then stop the loop. */
 int hlc_serve_stop(hlc_ctx* ctx);
 
 #ifdef __cplusplus

@@ -32,6 +32,18 @@ struct hlc_ctx {
   double* d_scratch = nullptr;
   cudaEvent_t ev[4];
   hlc::Serve* serve = nullptr;
+  // measurement
+  double* d_flops = nullptr;  // NOPTYPES algorithmic flop counters
+  bool profiling = false;
+  double launches = 0;
+  double op_launches[NOPTYPES] = {};
+  double op_ms[NOPTYPES] = {};
+  std::vector<cudaEvent_t> evpool;
+  struct Pending {
+    int type;
+    int ev;
+  };
+  std::vector<Pending> pending;
 };
 
 struct hlc_hmat {
@@ -60,7 +72,7 @@ struct hlc_tree {
   bool chol_ready = false, solve_ready = false;
   double* d_tmp = nullptr;
   int64_t tmp_cap = 0;
-  double* d_vec = nullptr;  // 5 n: W0 | X | Y | Z | XS
+  double* d_vec = nullptr;  // 6 n: W0 | X | Y | Z | XS | R
   hlc_hmat* wsC = nullptr;
   hlc_hmat* wsL = nullptr;
 };
@@ -111,6 +123,8 @@ int upload_plan(Plan& P) {
 }
 
 void free_plan(Plan& P) {
+  if (P.graph) cudaGraphExecDestroy(P.graph);
+  P.graph = nullptr;
   cudaFree(P.d_gemm);
   cudaFree(P.d_trsm);
   cudaFree(P.d_potrf);
@@ -133,7 +147,77 @@ int ensure_tmp(hlc_tree* t, int64_t doubles) {
   return HLC_OK;
 }
 
+// Optional per-launch timing (environment HLC_PROFILE=1): every launch is
+// synchronised and timed on the host; totals per op type and the slowest
+// launches are printed when the process exits.
+struct Prof {
+  bool on = false;
+  double ms[NOPTYPES] = {};
+  int64_t launches[NOPTYPES] = {}, ops[NOPTYPES] = {};
+  struct Slow {
+    double ms;
+    int type, wave;
+    int64_t count;
+  };
+  std::vector<Slow> slow;
+  Prof() { on = getenv("HLC_PROFILE") && getenv("HLC_PROFILE")[0] == '1'; }
+  ~Prof() {
+    if (!on) return;
+    static const char* nm[NOPTYPES] = {"potrf", "trsm", "gemm", "trunc", "truncC"};
+    for (int i = 0; i < NOPTYPES; ++i)
+      fprintf(stderr, "hlc-profile %-6s launches %9lld ops %11lld  %10.2f ms\n", nm[i], (long long)launches[i],
+              (long long)ops[i], ms[i]);
+    std::sort(slow.begin(), slow.end(), [](const Slow& a, const Slow& b) { return a.ms > b.ms; });
+    for (size_t i = 0; i < slow.size() && i < 12; ++i)
+      fprintf(stderr, "hlc-profile slow %-6s wave %6d ops %7lld %8.3f ms\n", nm[slow[i].type], slow[i].wave,
+              (long long)slow[i].count, slow[i].ms);
+  }
+} g_prof;
+
+bool same_bases(const Bases& a, const Bases& b) { return std::memcmp(&a, &b, sizeof(Bases)) == 0; }
+
+bool graphs_enabled() {
+  static const bool on = !(getenv("HLC_GRAPHS") && getenv("HLC_GRAPHS")[0] == '0');
+  return on;
+}
+
+void run_plan_launches(hlc_tree* t, const Plan& P, const Bases& B, cudaStream_t st, bool count);
+
+// Run a plan: replayed from a CUDA graph when possible (the op program is the
+// same for every evaluation on a tree; only the ranks in device memory vary),
+// captured on first use for a given set of base pointers.
 void run_plan(hlc_tree* t, const Plan& P, const Bases& B, cudaStream_t st) {
+  hlc_ctx* c = t->ctx;
+  if (c->profiling || g_prof.on || !graphs_enabled() || P.launches.empty()) {
+    run_plan_launches(t, P, B, st, true);
+    return;
+  }
+  if (!P.graph || !same_bases(P.graph_key, B)) {
+    if (P.graph) {
+      cudaGraphExecDestroy(P.graph);
+      P.graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      run_plan_launches(t, P, B, st, false);
+      if (cudaStreamEndCapture(st, &g) == cudaSuccess && g) {
+        if (cudaGraphInstantiate(&P.graph, g, 0) != cudaSuccess) P.graph = nullptr;
+        cudaGraphDestroy(g);
+      }
+    }
+    cudaGetLastError();
+    if (!P.graph) {  // capture unavailable: plain launches
+      run_plan_launches(t, P, B, st, true);
+      return;
+    }
+    P.graph_key = B;
+  }
+  cudaGraphLaunch(P.graph, st);
+  c->launches += (double)P.launches.size();
+  for (const Launch& L : P.launches) c->op_launches[L.type] += 1;
+}
+
+void run_plan_launches(hlc_tree* t, const Plan& P, const Bases& B, cudaStream_t st, bool count) {
   const int md = (int)std::max<int64_t>(t->T.max_dense_dim, t->T.leaf);
   for (const Launch& L : P.launches) {
     const void* ops = nullptr;
@@ -141,14 +225,46 @@ void run_plan(hlc_tree* t, const Plan& P, const Bases& B, cudaStream_t st) {
       case OP_GEMM: ops = P.d_gemm + L.first; break;
       case OP_TRSM: ops = P.d_trsm + L.first; break;
       case OP_POTRF: ops = P.d_potrf + L.first; break;
-      default: ops = P.d_trunc + L.first; break;
+      default: ops = P.d_trunc + L.first; break;  // OP_TRUNC, OP_TRUNC_BIG
     }
+    hlc_ctx* c = t->ctx;
+    if (count) {
+      c->launches += 1;
+      c->op_launches[L.type] += 1;
+    }
+    if (c->profiling) {
+      const int ev = (int)c->pending.size() * 2;
+      while ((int)c->evpool.size() < ev + 2) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        c->evpool.push_back(e);
+      }
+      cudaEventRecord(c->evpool[ev], st);
+      launch_ops(L.type, ops, L.count, P.d_terms, B, md, st);
+      cudaEventRecord(c->evpool[ev + 1], st);
+      c->pending.push_back(hlc_ctx::Pending{L.type, ev});
+      continue;
+    }
+    if (!g_prof.on) {
+      launch_ops(L.type, ops, L.count, P.d_terms, B, md, st);
+      continue;
+    }
+    cudaStreamSynchronize(st);
+    const auto t0 = std::chrono::steady_clock::now();
     launch_ops(L.type, ops, L.count, P.d_terms, B, md, st);
+    cudaStreamSynchronize(st);
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    g_prof.ms[L.type] += ms;
+    g_prof.launches[L.type] += 1;
+    g_prof.ops[L.type] += L.count;
+    if (g_prof.slow.size() < 4096 || ms > 1.0) g_prof.slow.push_back(Prof::Slow{ms, L.type, L.wave, L.count});
   }
 }
 
-Bases make_bases(hlc_tree* t, double* mat_L, double* mat_C, int* ranks) {
+Bases make_bases(hlc_tree* t, double* mat_L, double* mat_C, int* ranks, bool mixed) {
   Bases B;
+  B.mixed = mixed ? 1 : 0;
+  B.pad = 0;
   B.buf[BUF_L] = mat_L;
   B.buf[BUF_TMP] = t->d_tmp;
   B.buf[BUF_VEC] = t->d_vec;
@@ -156,6 +272,7 @@ Bases make_bases(hlc_tree* t, double* mat_L, double* mat_C, int* ranks) {
   B.ranks = ranks;
   B.status = t->ctx->d_status;
   B.scratch = t->ctx->d_scratch;
+  B.flops = t->ctx->d_flops;
   return B;
 }
 
@@ -222,7 +339,7 @@ int check_plan(hlc_tree* t, const Plan& P) {
   sz[BUF_L] = t->T.arena_doubles;
   sz[BUF_C] = t->T.arena_doubles;
   sz[BUF_TMP] = P.tmp_doubles;
-  sz[BUF_VEC] = 5 * t->T.n;
+  sz[BUF_VEC] = 6 * t->T.n;
   const std::string err = validate_plan(P, sz);
   if (!err.empty()) {
     fprintf(stderr, "hlc: plan rejected: %s\n", err.c_str());
@@ -267,9 +384,11 @@ int do_assemble(hlc_tree* t, const hlc_theta* th, hlc_hmat* C) {
   CK(cudaMemcpyAsync(t->d_knu, t->h_knu.data(), t->h_knu.size() * sizeof(double), cudaMemcpyHostToDevice,
                      c->stream));
   launch_dense_asm(t->d_dense, (int64_t)t->T.dense_asm.size(), C->arena, t->d_px, t->d_py, mp, c->stream);
-  launch_aca(t->d_lr, (int64_t)t->T.lr_asm.size(), C->arena, t->d_px, t->d_py, mp, t->p.eps, C->ranks,
+  c->launches += 2;  // dense assembly + ACA
+  const bool mixed = t->p.precision == HLC_MIXED;
+  launch_aca(t->d_lr, (int64_t)t->T.lr_asm.size(), C->arena, t->d_px, t->d_py, mp, t->p.eps, C->ranks, mixed,
              c->stream);
-  Bases B = make_bases(t, nullptr, C->arena, C->ranks);
+  Bases B = make_bases(t, nullptr, C->arena, C->ranks, mixed);
   run_plan(t, t->recomp, B, c->stream);
   CK(cudaGetLastError());
   C->valid = false;
@@ -286,7 +405,7 @@ int do_cholesky(hlc_tree* t, const hlc_hmat* C, hlc_hmat* L) {
                      c->stream));
   if (t->T.nslots)
     CK(cudaMemcpyAsync(L->ranks, C->ranks, t->T.nslots * sizeof(int), cudaMemcpyDeviceToDevice, c->stream));
-  Bases B = make_bases(t, L->arena, nullptr, L->ranks);
+  Bases B = make_bases(t, L->arena, nullptr, L->ranks, t->p.precision == HLC_MIXED);
   run_plan(t, t->chol, B, c->stream);
   CK(cudaGetLastError());
   L->valid = false;
@@ -326,7 +445,49 @@ void hmat_stats(hlc_tree* t, const hlc_hmat* M, size_t* bytes, int* maxr) {
 // ===========================================================================
 // C ABI
 // ===========================================================================
+namespace hlc {
+Serve*& serve_of(hlc_ctx* c) { return c->serve; }
+int device_of(hlc_ctx* c) { return c->device; }
+}  // namespace hlc
+
 extern "C" {
+
+int hlc_ctx_stream(hlc_ctx* c, void** stream) {
+  if (!c || !stream) return HLC_ERR_ARG;
+  *stream = (void*)c->stream;
+  return HLC_OK;
+}
+
+int hlc_ctx_set_profiling(hlc_ctx* c, int on) {
+  if (!c) return HLC_ERR_ARG;
+  c->profiling = on != 0;
+  return HLC_OK;
+}
+
+int hlc_ctx_counters(hlc_ctx* c, int reset, double* out) {
+  if (!c || !out) return HLC_ERR_ARG;
+  CK(cudaSetDevice(c->device));
+  CK(cudaStreamSynchronize(c->stream));
+  for (const hlc_ctx::Pending& p : c->pending) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, c->evpool[p.ev], c->evpool[p.ev + 1]) == cudaSuccess) c->op_ms[p.type] += ms;
+  }
+  c->pending.clear();
+  double fl[NOPTYPES];
+  CK(cudaMemcpy(fl, c->d_flops, sizeof(fl), cudaMemcpyDeviceToHost));
+  out[0] = c->launches;
+  for (int t = 0; t < NOPTYPES; ++t) {
+    out[1 + 3 * t] = c->op_launches[t];
+    out[2 + 3 * t] = c->op_ms[t];
+    out[3 + 3 * t] = fl[t];
+  }
+  if (reset) {
+    c->launches = 0;
+    for (int t = 0; t < NOPTYPES; ++t) c->op_launches[t] = c->op_ms[t] = 0;
+    CK(cudaMemset(c->d_flops, 0, NOPTYPES * sizeof(double)));
+  }
+  return HLC_OK;
+}
 
 void hlc_default_params(hlc_params* p) {
   if (!p) return;
@@ -335,7 +496,7 @@ void hlc_default_params(hlc_params* p) {
   p->eps = 1e-6;
   p->precision = HLC_FP64;
   p->refine_tol = 1e-12;
-  p->refine_maxit = 30;
+  p->refine_maxit = 100;
   p->kmax = 64;
 }
 
@@ -372,6 +533,8 @@ int hlc_create(hlc_ctx** out, int device) {
   if (e == cudaSuccess) e = cudaMalloc(&c->d_part, 1 << 20);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_scalar, 64);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_status, 16);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_flops, NOPTYPES * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(c->d_flops, 0, NOPTYPES * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, 16);
   if (e == cudaSuccess)
     e = cudaMalloc(&c->d_scratch, (size_t)max_trunc_ctas() * trunc_scratch_doubles() * sizeof(double));
@@ -385,14 +548,28 @@ int hlc_create(hlc_ctx** out, int device) {
   return HLC_OK;
 }
 
+// After the CUDA runtime has begun unloading (process exit), device
+// resources are gone with the context: release host memory only.
+static bool runtime_alive(int device) {
+  const cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) return true;
+  cudaGetLastError();
+  return false;
+}
+
 void hlc_destroy(hlc_ctx* c) {
   if (!c) return;
-  cudaSetDevice(c->device);
+  if (!runtime_alive(c->device)) {
+    delete c;
+    return;
+  }
   if (c->serve) hlc_serve_stop(c);
   cudaFree(c->d_part);
   cudaFree(c->d_scalar);
   cudaFree(c->d_status);
   cudaFree(c->d_scratch);
+  cudaFree(c->d_flops);
+  for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
   for (int i = 0; i < 4; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
   if (c->stream) cudaStreamDestroy(c->stream);
@@ -406,7 +583,7 @@ int hlc_build_tree(hlc_ctx* c, const double* xy, int64_t n, const hlc_params* p,
     q = *p;
   else
     hlc_default_params(&q);
-  if (q.leaf < 1 || q.leaf > 128 || !(q.eta > 0.0) || !(q.eps > 0.0) || q.kmax < 1 || q.kmax > 64 ||
+  if (q.leaf < 1 || q.leaf > 128 || !(q.eta > 0.0) || !(q.eps > 0.0) || q.kmax < 1 || q.kmax > 128 ||
       (q.precision != HLC_FP64 && q.precision != HLC_MIXED) || q.refine_maxit < 0)
     return HLC_ERR_ARG;
   *out = nullptr;
@@ -415,32 +592,45 @@ int hlc_build_tree(hlc_ctx* c, const double* xy, int64_t n, const hlc_params* p,
   if (!t) return HLC_ERR_OOM;
   t->ctx = c;
   t->p = q;
-  // points to the host for the structure, to the device for the kernels
-  std::vector<double> hxy((size_t)2 * n);
+  // points on the device; the trees are built there (Morton sort, bisection,
+  // block-cluster tree) and their structure copied to the host planner
+  const bool host_tree = getenv("HLC_HOST_TREE") && getenv("HLC_HOST_TREE")[0] == '1';
   double* d_xy = nullptr;
-  if (is_device_ptr(xy)) {
-    CK(cudaMemcpy(hxy.data(), xy, 2 * n * sizeof(double), cudaMemcpyDeviceToHost));
-  } else {
-    std::memcpy(hxy.data(), xy, 2 * n * sizeof(double));
-  }
-  std::vector<double> hx(n), hy(n);
-  for (int64_t i = 0; i < n; ++i) {
-    hx[i] = hxy[2 * i];
-    hy[i] = hxy[2 * i + 1];
-  }
+  CK(cudaMalloc(&d_xy, 2 * n * sizeof(double)));
+  CK(cudaMemcpy(d_xy, xy, 2 * n * sizeof(double), is_device_ptr(xy) ? cudaMemcpyDeviceToDevice
+                                                                    : cudaMemcpyHostToDevice));
   try {
-    tree_from_points(t->T, hx.data(), hy.data(), n, q.leaf, q.eta);
+    t->T.n = n;
+    t->T.leaf = q.leaf;
+    t->T.eta = q.eta;
     t->T.eps = q.eps;
-    block_tree(t->T);
+    if (host_tree) {
+      std::vector<double> hxy((size_t)2 * n), hx(n), hy(n);
+      CK(cudaMemcpy(hxy.data(), d_xy, 2 * n * sizeof(double), cudaMemcpyDeviceToHost));
+      for (int64_t i = 0; i < n; ++i) {
+        hx[i] = hxy[2 * i];
+        hy[i] = hxy[2 * i + 1];
+      }
+      tree_from_points(t->T, hx.data(), hy.data(), n, q.leaf, q.eta);
+      block_tree(t->T);
+    } else {
+      int depth = 0;
+      if (device_tree_build(d_xy, n, q.leaf, q.eta, c->stream, t->T.perm, t->T.cl, t->T.blk, &depth) != 0) {
+        cudaFree(d_xy);
+        return HLC_ERR_CUDA;
+      }
+      t->T.depth = depth;
+      collect_leaf_list(t->T);
+    }
+    t->T.eps = q.eps;
     layout(t->T, q.kmax);
     plan_recompress(t->T, t->recomp);
   } catch (const std::bad_alloc&) {
+    cudaFree(d_xy);
     return HLC_ERR_OOM;
   }
   int st;
   if ((st = upload(&t->d_perm, t->T.perm))) return st;
-  CK(cudaMalloc(&d_xy, 2 * n * sizeof(double)));
-  CK(cudaMemcpy(d_xy, hxy.data(), 2 * n * sizeof(double), cudaMemcpyHostToDevice));
   CK(cudaMalloc(&t->d_px, n * sizeof(double)));
   CK(cudaMalloc(&t->d_py, n * sizeof(double)));
   launch_points(d_xy, t->d_perm, t->d_px, t->d_py, n, c->stream);
@@ -461,7 +651,7 @@ int hlc_build_tree(hlc_ctx* c, const double* xy, int64_t n, const hlc_params* p,
   if ((st = upload(&t->d_diag_off, doff))) return st;
   if ((st = upload(&t->d_diag_dim, ddim))) return st;
   CK(cudaMalloc(&t->d_knu, 2 * KNU_NODES * sizeof(double)));
-  CK(cudaMalloc(&t->d_vec, 5 * n * sizeof(double)));
+  CK(cudaMalloc(&t->d_vec, 6 * n * sizeof(double)));
   if ((st = check_plan(t.get(), t->recomp))) return st;
   if ((st = upload_plan(t->recomp))) return st;
   if ((st = ensure_tmp(t.get(), t->recomp.tmp_doubles))) return st;
@@ -471,7 +661,10 @@ int hlc_build_tree(hlc_ctx* c, const double* xy, int64_t n, const hlc_params* p,
 
 void hlc_tree_free(hlc_tree* t) {
   if (!t) return;
-  cudaSetDevice(t->ctx->device);
+  if (!runtime_alive(t->ctx->device)) {
+    delete t;
+    return;
+  }
   cudaStreamSynchronize(t->ctx->stream);
   hlc_hmat_free(t->wsC);
   hlc_hmat_free(t->wsL);
@@ -582,7 +775,7 @@ int hlc_matvec(hlc_ctx* c, const hlc_hmat* C, const double* x, double* y) {
     launch_gather(S, t->d_perm, X, n, c->stream);
   }
   CK(cudaMemsetAsync(Y, 0, n * sizeof(double), c->stream));
-  Bases B = make_bases(t, nullptr, C->arena, C->ranks);
+  Bases B = make_bases(t, nullptr, C->arena, C->ranks, false);
   run_plan(t, t->mv, B, c->stream);
   if (dy) {
     launch_scatter(Y, t->d_perm, y, n, c->stream);
@@ -645,6 +838,10 @@ int hlc_hmat_ranks(hlc_ctx* c, const hlc_hmat* M, int32_t* out) {
 
 void hlc_hmat_free(hlc_hmat* M) {
   if (!M) return;
+  if (!runtime_alive(M->t->ctx->device)) {
+    delete M;
+    return;
+  }
   cudaFree(M->arena);
   cudaFree(M->ranks);
   delete M;
@@ -668,46 +865,96 @@ int hlc_loglik(hlc_ctx* c, hlc_tree* t, const hlc_theta* th, const double* z, hl
   // data vector to tree order
   if (is_device_ptr(z)) {
     launch_gather(z, t->d_perm, Z, n, s);
+    c->launches += 1;
   } else {
     CK(cudaMemcpyAsync(Y, z, n * sizeof(double), cudaMemcpyHostToDevice, s));
     launch_gather(Y, t->d_perm, Z, n, s);
+    c->launches += 1;
   }
   CK(cudaEventRecord(c->ev[0], s));
   if ((st = do_assemble(t, th, t->wsC))) return st;
   CK(cudaEventRecord(c->ev[1], s));
   if ((st = do_cholesky(t, t->wsC, t->wsL))) return st;
   CK(cudaEventRecord(c->ev[2], s));
-  Bases BL = make_bases(t, t->wsL->arena, nullptr, t->wsL->ranks);
-  Bases BC = make_bases(t, nullptr, t->wsC->arena, t->wsC->ranks);
-  // log det = 2 sum log L_ii
+  // the preconditioner solves follow the factor's precision; the residual
+  // matvec against C~ is always FP64
+  Bases BL = make_bases(t, t->wsL->arena, nullptr, t->wsL->ranks, t->p.precision == HLC_MIXED);
+  Bases BC = make_bases(t, nullptr, t->wsC->arena, t->wsC->ranks, false);
+  // log det = 2 sum log L_ii  (2 launches), and the vector kernels below
+  c->launches += 2;
   launch_logdet(t->d_diag_off, t->d_diag_dim, t->ndiag, t->wsL->arena, c->d_part, c->d_scalar + 0, s);
   // v = L^-1 z, quad_factor = v^T v, x = L^-T v
   CK(cudaMemcpyAsync(W0, Z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   run_plan(t, t->fwd, BL, s);
   launch_dot(W0, W0, n, c->d_part, c->d_scalar + 1, s);
+  c->launches += 2;
   run_plan(t, t->bwd, BL, s);
   CK(cudaMemcpyAsync(XS, W0, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   launch_dot(Z, Z, n, c->d_part, c->d_scalar + 2, s);
+  c->launches += 2;
   const double logdet_half = read_scalar(c, 0);
   const double qf = read_scalar(c, 1);
   const double zn = sqrt(read_scalar(c, 2));
-  // FP64 refinement against C~: x += (L L^T)^-1 (z - C~ x)
-  int it = 0;
-  double rel = 0.0;
-  for (;;) {
-    CK(cudaMemcpyAsync(X, XS, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemsetAsync(Y, 0, n * sizeof(double), s));
+  // Quadratic form: conjugate gradients on C~ preconditioned with
+  // (L~ L~^T)^-1, started from x0 = (L~ L~^T)^-1 z (App. B listing).
+  // vectors: XS = x, X = p (matvec input), Y = C~ p, W0 = preconditioned r,
+  // R = residual (tree workspace slot 5).
+  double* R = t->d_vec + 5 * n;
+  auto matvec = [&](double* in) {
+    if (in != X) cudaMemcpyAsync(X, in, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    cudaMemsetAsync(Y, 0, n * sizeof(double), s);
     run_plan(t, t->mv, BC, s);
-    launch_sub(Z, Y, W0, n, s);
-    launch_dot(W0, W0, n, c->d_part, c->d_scalar + 3, s);
-    rel = zn > 0.0 ? sqrt(read_scalar(c, 3)) / zn : 0.0;
-    if (!(rel > t->p.refine_tol) || it >= t->p.refine_maxit) break;
+  };
+  matvec(XS);
+  launch_sub(Z, Y, R, n, s);
+  c->launches += 1;
+  launch_dot(R, R, n, c->d_part, c->d_scalar + 3, s);
+  c->launches += 2;
+  int it = 0;
+  double rel = zn > 0.0 ? sqrt(read_scalar(c, 3)) / zn : 0.0;
+  if (rel > t->p.refine_tol && t->p.refine_maxit > 0) {
+    CK(cudaMemcpyAsync(W0, R, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     run_plan(t, t->fwd, BL, s);
     run_plan(t, t->bwd, BL, s);
-    launch_axpby(1.0, W0, 1.0, XS, n, s);
-    ++it;
+    CK(cudaMemcpyAsync(X, W0, n * sizeof(double), cudaMemcpyDeviceToDevice, s));  // p = w
+    launch_dot(R, W0, n, c->d_part, c->d_scalar + 5, s);
+    c->launches += 2;
+    double rw = read_scalar(c, 5);
+    while (it < t->p.refine_maxit) {
+      matvec(X);  // Y = C p
+      launch_dot(X, Y, n, c->d_part, c->d_scalar + 6, s);
+      c->launches += 2;
+      const double alpha = rw / read_scalar(c, 6);
+      launch_axpby(alpha, X, 1.0, XS, n, s);
+      c->launches += 1;
+      launch_axpby(-alpha, Y, 1.0, R, n, s);
+      c->launches += 1;
+      ++it;
+      launch_dot(R, R, n, c->d_part, c->d_scalar + 3, s);
+      c->launches += 2;
+      rel = zn > 0.0 ? sqrt(read_scalar(c, 3)) / zn : 0.0;
+      if (!(rel > t->p.refine_tol)) break;
+      CK(cudaMemcpyAsync(W0, R, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      run_plan(t, t->fwd, BL, s);
+      run_plan(t, t->bwd, BL, s);
+      launch_dot(R, W0, n, c->d_part, c->d_scalar + 5, s);
+      c->launches += 2;
+      const double rw1 = read_scalar(c, 5);
+      const double beta = rw1 / rw;
+      rw = rw1;
+      launch_axpby(1.0, W0, beta, X, n, s);
+      c->launches += 1;  // p = w + beta p
+    }
+    // true residual at exit
+    matvec(XS);
+    launch_sub(Z, Y, R, n, s);
+    c->launches += 1;
+    launch_dot(R, R, n, c->d_part, c->d_scalar + 3, s);
+    c->launches += 2;
+    rel = zn > 0.0 ? sqrt(read_scalar(c, 3)) / zn : 0.0;
   }
   launch_dot(Z, XS, n, c->d_part, c->d_scalar + 4, s);
+  c->launches += 2;
   const double quad = read_scalar(c, 4);
   CK(cudaEventRecord(c->ev[3], s));
   CK(cudaEventSynchronize(c->ev[3]));

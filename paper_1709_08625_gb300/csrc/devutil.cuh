@@ -1,0 +1,87 @@
+// devutil.cuh -- small device helpers shared by the kernel files.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "hlc_internal.h"
+
+namespace hlc {
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int dimv(const Dim& d, const int* ranks) {
+  if (d.slot < 0) return d.n;
+  const int r = ranks[d.slot];
+  return r < d.n ? r : d.n;
+}
+
+__device__ __forceinline__ double* vptr(const Bases& B, const Mv& v) { return B.buf[v.buf] + v.off; }
+
+__device__ __forceinline__ void record_error(int* status, int code, int detail) {
+  if (atomicCAS(status, 0, code) == 0) status[1] = detail;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum; all threads get the result.  `red` needs 33 doubles.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    double t = lane < nw ? red[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) red[32] = t;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// Block-wide argmax of |value| with ties to the smaller index; returns the
+// index (or -1 when every candidate is excluded) and the value in *best.
+__device__ __forceinline__ int block_argmax(double v, int idx, double* redv, int* redi, double* best) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (ov > v || (ov == v && oi >= 0 && (idx < 0 || oi < idx))) {
+      v = ov;
+      idx = oi;
+    }
+  }
+  __syncthreads();
+  if (lane == 0) {
+    redv[w] = v;
+    redi[w] = idx;
+  }
+  __syncthreads();
+  if (w == 0) {
+    v = lane < nw ? redv[lane] : -1.0;
+    idx = lane < nw ? redi[lane] : -1;
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+      if (ov > v || (ov == v && oi >= 0 && (idx < 0 || oi < idx))) {
+        v = ov;
+        idx = oi;
+      }
+    }
+    if (lane == 0) {
+      redv[32] = v;
+      redi[32] = idx;
+    }
+  }
+  __syncthreads();
+  *best = redv[32];
+  return redi[32];
+}
+
+}  // namespace hlc

@@ -208,6 +208,11 @@ void block_tree(HTree& T) {
   collect_leaves(T, 0);
 }
 
+void collect_leaf_list(HTree& T) {
+  T.leaves.clear();
+  collect_leaves(T, 0);
+}
+
 void layout(HTree& T, int kmax) {
   T.kmax = kmax;
   int64_t off = 0;
@@ -279,6 +284,18 @@ struct PV {
 
 const int32_t NOSLOT = -1;
 
+struct TermP {
+  PV U, V;
+  int64_t urows, vrows;
+  int64_t roff, coff;
+  Dim k;
+  int32_t flags;
+  double alpha;
+};
+const int64_t kTruncBigRows = 4096;   // m + n above which a truncation uses a cluster
+const int64_t kGemmSplitRows = 4096;  // row block of a split product
+const int64_t kPendingCols = INT64_MAX;  // no size-forced truncation: flush only on use
+
 struct Planner {
   HTree& T;
   Plan& P;
@@ -294,10 +311,19 @@ struct Planner {
   std::vector<Ref> seq;
   int32_t maxwave = -1;
 
+  // Accumulated updates: terms added to a low-rank block wait here and are
+  // truncated together (in batches of 64 columns) right before the block is
+  // read or written otherwise, or when too many columns have piled up.
+  bool defer = false;
+  std::vector<std::vector<struct TermP>> pending;
+  std::vector<int64_t> pending_cols;
+
   Planner(HTree& t, Plan& p, int32_t mbuf) : T(t), P(p), mat_buf(mbuf) {
     objD.assign(T.blk.size(), -1);
     objU.assign(T.blk.size(), -1);
     objV.assign(T.blk.size(), -1);
+    pending.assign(T.blk.size(), {});
+    pending_cols.assign(T.blk.size(), 0);
     for (int32_t b : T.leaves) {
       const Block& B = T.blk[b];
       if (B.type == BT_DENSE) {
@@ -465,6 +491,14 @@ struct Planner {
   // ---- op emission ----
   void gemm(const PV& Y, const PV& A, const PV& B, Dim m, Dim k, Dim c, double alpha) {
     if (m.n <= 0 || c.n <= 0 || k.n <= 0) return;
+    // tall products split into independent row blocks (one CTA each)
+    if (m.slot < 0 && m.n > kGemmSplitRows) {
+      for (int64_t r0 = 0; r0 < m.n; r0 += kGemmSplitRows) {
+        const int64_t r1 = std::min<int64_t>(m.n, r0 + kGemmSplitRows);
+        gemm(rows(Y, r0, r1), rows(A, r0, r1), B, dim(r1 - r0, NOSLOT), k, c, alpha);
+      }
+      return;
+    }
     OpGemm op;
     op.Y = mv(Y);
     op.A = mv(A);
@@ -520,15 +554,6 @@ struct Planner {
     seq.push_back(Ref{OP_POTRF, (int64_t)P.potrf.size() - 1, w});
   }
 
-  struct TermP {
-    PV U, V;
-    int64_t urows, vrows;
-    int64_t roff, coff;
-    Dim k;
-    int32_t flags;
-    double alpha;
-  };
-
   void trunc(int32_t b, const std::vector<TermP>& terms, int keep) {
     const Block& B = T.blk[b];
     OpTrunc op;
@@ -562,7 +587,38 @@ struct Planner {
     }
     const int32_t w = place(reads, {U, V});
     P.trunc.push_back(op);
-    seq.push_back(Ref{OP_TRUNC, (int64_t)P.trunc.size() - 1, w});
+    // large targets run on a thread-block cluster
+    const int32_t ty = (B.m + B.n > kTruncBigRows) ? OP_TRUNC_BIG : OP_TRUNC;
+    seq.push_back(Ref{ty, (int64_t)P.trunc.size() - 1, w});
+  }
+
+  static int64_t term_cap(const TermP& t) {
+    return (t.flags & 1) ? t.urows : (t.flags & 2) ? t.vrows : t.k.n;
+  }
+  void add_terms(int32_t c, const std::vector<TermP>& terms) {
+    if (!defer) {
+      trunc(c, terms, 1);
+      return;
+    }
+    for (const TermP& t : terms) {
+      pending[c].push_back(t);
+      pending_cols[c] += term_cap(t);
+    }
+    if (pending_cols[c] > kPendingCols) flush(c);
+  }
+  void flush(int32_t b) {
+    if (b < 0 || pending[b].empty()) return;
+    std::vector<TermP> terms;
+    terms.swap(pending[b]);
+    pending_cols[b] = 0;
+    trunc(b, terms, 1);
+  }
+  void flush_all() {
+    for (size_t b = 0; b < pending.size(); ++b) flush((int32_t)b);
+  }
+  // a leaf block is about to be read (or rewritten): its pending updates first
+  void use(int32_t b) {
+    if (T.blk[b].type == BT_LR) flush(b);
   }
 
   // ---- block views ----
@@ -578,6 +634,7 @@ struct Planner {
 
   // Y += alpha * A X  (A off-diagonal)
   void hmul(int32_t a, const PV& X, const PV& Y, double alpha) {
+    use(a);
     const Block& A = blk(a);
     const Dim c = dim(X.cols, X.dcol);
     if (A.type == BT_DENSE) {
@@ -601,6 +658,7 @@ struct Planner {
 
   // Y += alpha * A^T X  (A off-diagonal)
   void hmul_t(int32_t a, const PV& X, const PV& Y, double alpha) {
+    use(a);
     const Block& A = blk(a);
     const Dim c = dim(X.cols, X.dcol);
     if (A.type == BT_DENSE) {
@@ -663,7 +721,7 @@ struct Planner {
       gemm(D(c), Uv, T_(Vv), dim(C.m, NOSLOT), k, dim(C.n, NOSLOT), alpha);
     } else if (C.type == BT_LR) {
       TermP t{Uv, Vv, C.m, C.n, 0, 0, k, 0, alpha};
-      trunc(c, {t}, 1);
+      add_terms(c, {t});
     } else {
       const int64_t r0 = rlo(c), s0 = slo(c);
       for (int q = 0; q < 4; ++q) {
@@ -698,7 +756,7 @@ struct Planner {
         t.flags = 2;
         t.k = dim(C.n, NOSLOT);
       }
-      trunc(c, {t}, 1);
+      add_terms(c, {t});
     } else {
       const int64_t r0 = rlo(c), s0 = slo(c);
       for (int q = 0; q < 4; ++q) {
@@ -713,6 +771,8 @@ struct Planner {
 
   // exact product A B^T as low-rank terms inside the |r| x |r'| target
   void prod_terms(int32_t a, int32_t b, int64_t roff, int64_t coff, double alpha, std::vector<TermP>& out) {
+    use(a);
+    use(b);
     const Block& A = blk(a);
     const Block& B = blk(b);
     if (A.type == BT_LR) {
@@ -750,6 +810,8 @@ struct Planner {
 
   // C += alpha A B^T with truncation; A = (r, s), B = (r', s), C = (r, r')
   void mul_add(int32_t c, int32_t a, int32_t b, double alpha) {
+    use(a);
+    use(b);
     const Block& A = blk(a);
     const Block& B = blk(b);
     const Block& C = blk(c);
@@ -794,7 +856,7 @@ struct Planner {
       std::vector<TermP> terms;
       prod_terms(a, b, 0, 0, alpha, terms);
       if (C.type == BT_LR) {
-        trunc(c, terms, 1);
+        add_terms(c, terms);
       } else {
         // not reachable for geometric trees (a dense target has a leaf
         // cluster); expand the terms into a temporary and add it
@@ -816,6 +878,7 @@ struct Planner {
 
   // B := B L^-T
   void trsm_blk(int32_t l, int32_t b) {
+    use(b);
     const Block& B = blk(b);
     if (B.type == BT_DENSE) {
       trsv(l, T_(D(b)));
@@ -969,14 +1032,14 @@ struct Planner {
         case OP_GEMM: pos = (int64_t)g.size(); g.push_back(P.gemm[r.idx]); break;
         case OP_TRSM: pos = (int64_t)t.size(); t.push_back(P.trsm[r.idx]); break;
         case OP_POTRF: pos = (int64_t)p.size(); p.push_back(P.potrf[r.idx]); break;
-        default: pos = (int64_t)u.size(); u.push_back(P.trunc[r.idx]); break;
+        default: pos = (int64_t)u.size(); u.push_back(P.trunc[r.idx]); break;  // OP_TRUNC, OP_TRUNC_BIG
       }
       if (!P.launches.empty() && P.launches.back().wave == r.wave && P.launches.back().type == r.type) {
         P.launches.back().count++;
       } else {
         P.launches.push_back(Launch{r.type, r.wave, pos, 1});
       }
-      if (r.type == OP_TRUNC) P.max_trunc_per_wave = std::max(P.max_trunc_per_wave, P.launches.back().count);
+      if (r.type == OP_TRUNC || r.type == OP_TRUNC_BIG) P.max_trunc_per_wave = std::max(P.max_trunc_per_wave, P.launches.back().count);
     }
     P.gemm.swap(g);
     P.trsm.swap(t);
@@ -987,10 +1050,12 @@ struct Planner {
 
 }  // namespace
 
-void plan_cholesky(HTree& T, Plan& P) {
+void plan_cholesky(HTree& T, Plan& P, bool accumulate) {
   P = Plan();
   Planner pl(T, P, BUF_L);
+  pl.defer = accumulate;
   pl.chol(0);
+  pl.flush_all();
   pl.finish();
 }
 
@@ -1068,7 +1133,7 @@ std::string validate_plan(const Plan& P, const int64_t* bufsize) {
   }
   for (size_t i = 0; i < P.trunc.size(); ++i) {
     const OpTrunc& t = P.trunc[i];
-    if (t.kcap > 64) return "trunc: rank capacity above 64";
+    if (t.kcap > 128) return "trunc: rank capacity above 128";
     if (!check(t.U, t.m, t.kcap, "trunc.U", i) || !check(t.V, t.n, t.kcap, "trunc.V", i)) return msg;
     if (t.term0 < 0 || t.term0 + t.nterms > (int64_t)P.terms.size()) return "trunc: term range";
     for (int q = 0; q < t.nterms; ++q) {

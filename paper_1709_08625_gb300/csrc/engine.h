@@ -29,10 +29,14 @@ void tree_from_points(HTree& T, const double* x, const double* y, int64_t n, int
 bool is_admissible(const HTree& T, int r, int s);
 // Block-cluster tree over the lower triangle, leaves depth-first.
 void block_tree(HTree& T);
+// Leaf list (depth-first) of a block tree built elsewhere (device build).
+void collect_leaf_list(HTree& T);
 // Arena offsets, rank capacities and rank slots of the leaves.
 void layout(HTree& T, int kmax);
 
-void plan_cholesky(HTree& T, Plan& P);
+// accumulate: updates of a low-rank block are truncated together right before
+// the block is next used (accumulated updates) instead of one at a time.
+void plan_cholesky(HTree& T, Plan& P, bool accumulate = true);
 void plan_solve(HTree& T, Plan& P, int trans, int64_t voff, int64_t ncols);
 void plan_matvec(HTree& T, Plan& P, int64_t xoff, int64_t yoff, int64_t ncols);
 void plan_recompress(HTree& T, Plan& P);

@@ -94,9 +94,12 @@ struct Bases {
   int* ranks;      // rank slots of the matrix in BUF_L
   int* status;     // [0] error code, [1] detail (first error wins)
   double* scratch; // per-CTA scratch of the truncation kernel
+  int mixed;       // 1: FP32 arithmetic for panels, products and QR (HLC_MIXED)
+  int pad;
+  double* flops;   // per op type algorithmic flop counters, or null
 };
 
-enum OpType : int32_t { OP_POTRF = 0, OP_TRSM = 1, OP_GEMM = 2, OP_TRUNC = 3, NOPTYPES = 4 };
+enum OpType : int32_t { OP_POTRF = 0, OP_TRSM = 1, OP_GEMM = 2, OP_TRUNC = 3, OP_TRUNC_BIG = 4, NOPTYPES = 5 };
 
 // Device error codes recorded in status[0].
 enum DevErr : int32_t { DEV_OK = 0, DEV_NOT_SPD = 1, DEV_RANK = 2, DEV_BAD = 3 };
@@ -160,6 +163,10 @@ struct Plan {
   int32_t nwaves = 0;
   int64_t max_trunc_per_wave = 0;
   bool checked = false;
+  // the plan captured as a CUDA graph for one set of base pointers
+  mutable cudaGraphExec_t graph = nullptr;
+  mutable Bases graph_key{};
+  mutable int64_t graph_kernels = 0;
   // device copies
   OpGemm* d_gemm = nullptr;
   OpTrsm* d_trsm = nullptr;

@@ -19,83 +19,9 @@
 #include "hlc_internal.h"
 #include "kernels.h"
 #include "matern.cuh"
+#include "devutil.cuh"
 
 namespace hlc {
-
-// ---------------------------------------------------------------------------
-// helpers
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ int dimv(const Dim& d, const int* ranks) {
-  if (d.slot < 0) return d.n;
-  const int r = ranks[d.slot];
-  return r < d.n ? r : d.n;
-}
-
-__device__ __forceinline__ double* vptr(const Bases& B, const Mv& v) { return B.buf[v.buf] + v.off; }
-
-__device__ void record_error(int* status, int code, int detail) {
-  if (atomicCAS(status, 0, code) == 0) status[1] = detail;
-}
-
-__device__ __forceinline__ double warp_sum(double v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Block-wide sum; all threads get the result.  `red` needs 33 doubles.
-__device__ double block_sum(double v, double* red) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  v = warp_sum(v);
-  __syncthreads();
-  if (lane == 0) red[w] = v;
-  __syncthreads();
-  if (w == 0) {
-    double t = lane < nw ? red[lane] : 0.0;
-    t = warp_sum(t);
-    if (lane == 0) red[32] = t;
-  }
-  __syncthreads();
-  return red[32];
-}
-
-// Block-wide argmax of |value| with ties to the smaller index; returns the
-// index (or -1 when every candidate is excluded) and the value in *best.
-__device__ int block_argmax(double v, int idx, double* redv, int* redi, double* best) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  for (int o = 16; o > 0; o >>= 1) {
-    const double ov = __shfl_xor_sync(0xffffffffu, v, o);
-    const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-    if (ov > v || (ov == v && oi >= 0 && (idx < 0 || oi < idx))) {
-      v = ov;
-      idx = oi;
-    }
-  }
-  __syncthreads();
-  if (lane == 0) {
-    redv[w] = v;
-    redi[w] = idx;
-  }
-  __syncthreads();
-  if (w == 0) {
-    v = lane < nw ? redv[lane] : -1.0;
-    idx = lane < nw ? redi[lane] : -1;
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_xor_sync(0xffffffffu, v, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-      if (ov > v || (ov == v && oi >= 0 && (idx < 0 || oi < idx))) {
-        v = ov;
-        idx = oi;
-      }
-    }
-    if (lane == 0) {
-      redv[32] = v;
-      redi[32] = idx;
-    }
-  }
-  __syncthreads();
-  *best = redv[32];
-  return redi[32];
-}
 
 // ---------------------------------------------------------------------------
 // Assembly
@@ -123,6 +49,21 @@ constexpr int ACA_THREADS = 256;
 // |u_k| |v_k| <= eps |S_k|_F (running Frobenius norm of the approximant).
 // A vanishing pivot row moves to the first unused row, at most three times
 // in a row.  Used rows and columns are excluded from the pivot searches.
+// T = float evaluates the kernel and the residuals in FP32 (HLC_MIXED); the
+// panels are stored in FP64 either way.
+template <class T>
+__device__ __forceinline__ T aca_entry(double x0, double y0, double x1, double y1, const MaternDev& mp);
+template <>
+__device__ __forceinline__ double aca_entry<double>(double x0, double y0, double x1, double y1, const MaternDev& mp) {
+  return matern_f64(dist_f64(x0, y0, x1, y1), mp);
+}
+template <>
+__device__ __forceinline__ float aca_entry<float>(double x0, double y0, double x1, double y1, const MaternDev& mp) {
+  const float dx = (float)(x0 - x1), dy = (float)(y0 - y1);
+  return matern_f32(sqrtf(dx * dx + dy * dy), mp);
+}
+
+template <class T>
 __global__ void __launch_bounds__(ACA_THREADS) k_aca(const LrAsm* blks, int64_t count, double* arena,
                                                       const double* px, const double* py, MaternDev mp,
                                                       double eps, int* ranks) {
@@ -151,12 +92,12 @@ __global__ void __launch_bounds__(ACA_THREADS) k_aca(const LrAsm* blks, int64_t 
       int bj = -1;
       const double xi = px[b.r0 + i], yi = py[b.r0 + i];
       for (int j = tid; j < n; j += blockDim.x) {
-        double v = matern_f64(dist_f64(xi, yi, px[b.c0 + j], py[b.c0 + j]), mp);
-        for (int l = 0; l < k; ++l) v -= s_ui[l] * V[j + (int64_t)l * n];
-        V[j + (int64_t)k * n] = v;
+        T v = aca_entry<T>(xi, yi, px[b.c0 + j], py[b.c0 + j], mp);
+        for (int l = 0; l < k; ++l) v -= (T)s_ui[l] * (T)V[j + (int64_t)l * n];
+        V[j + (int64_t)k * n] = (double)v;
         bool used = false;
         for (int q = 0; q < nuc; ++q) used |= (used_c[q] == j);
-        const double a = fabs(v);
+        const double a = fabs((double)v);
         if (!used && (a > best || (a == best && (bj < 0 || j < bj)))) {
           best = a;
           bj = j;
@@ -182,7 +123,7 @@ __global__ void __launch_bounds__(ACA_THREADS) k_aca(const LrAsm* blks, int64_t 
       __syncthreads();
       const double piv = V[jp + (int64_t)k * n];
       __syncthreads();
-      for (int j = tid; j < n; j += blockDim.x) V[j + (int64_t)k * n] /= piv;
+      for (int j = tid; j < n; j += blockDim.x) V[j + (int64_t)k * n] = (double)((T)V[j + (int64_t)k * n] / (T)piv);
       if (tid < k) s_vj[tid] = V[jp + (int64_t)tid * n];
       if (tid == 0) used_c[nuc] = jp;
       __syncthreads();
@@ -190,9 +131,9 @@ __global__ void __launch_bounds__(ACA_THREADS) k_aca(const LrAsm* blks, int64_t 
       // residual column jp into U[:, k]
       const double xj = px[b.c0 + jp], yj = py[b.c0 + jp];
       for (int t = tid; t < m; t += blockDim.x) {
-        double u = matern_f64(dist_f64(px[b.r0 + t], py[b.r0 + t], xj, yj), mp);
-        for (int l = 0; l < k; ++l) u -= U[t + (int64_t)l * m] * s_vj[l];
-        U[t + (int64_t)k * m] = u;
+        T u = aca_entry<T>(px[b.r0 + t], py[b.r0 + t], xj, yj, mp);
+        for (int l = 0; l < k; ++l) u -= (T)U[t + (int64_t)l * m] * (T)s_vj[l];
+        U[t + (int64_t)k * m] = (double)u;
       }
       __syncthreads();
       // norms: |u|^2, |v|^2 and the cross terms (U_l . u)(V_l . v)
@@ -271,6 +212,7 @@ __global__ void k_potrf(const OpPotrf* ops, int64_t count, Bases B) {
   for (int64_t o = blockIdx.x; o < count; o += gridDim.x) {
     const OpPotrf op = ops[o];
     const int n = op.n;
+    if (B.flops && threadIdx.x == 0) atomicAdd(B.flops + OP_POTRF, (double)n * n * n / 3.0);
     double* A = vptr(B, op.A);
     const int64_t ld = op.A.cs;
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
@@ -325,6 +267,7 @@ __global__ void k_trsm(const OpTrsm* ops, int64_t count, Bases B) {
     const OpTrsm op = ops[o];
     const int n = op.n;
     const int c = dimv(op.c, B.ranks);
+    if (B.flops && threadIdx.x == 0) atomicAdd(B.flops + OP_TRSM, (double)n * n * c);
     const double* L = vptr(B, op.L);
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
       const int i = e % n, j = e / n;
@@ -383,14 +326,17 @@ __global__ void k_trsm(const OpTrsm* ops, int64_t count, Bases B) {
 // ---------------------------------------------------------------------------
 constexpr int GB_M = 64, GB_N = 32, GB_K = 16;
 
+template <class T>
 __global__ void __launch_bounds__(256) k_gemm(const OpGemm* ops, int64_t count, Bases B) {
-  __shared__ double As[GB_K][GB_M + 1];
-  __shared__ double Bs[GB_K][GB_N + 1];
+  __shared__ T As[GB_K][GB_M + 1];
+  __shared__ T Bs[GB_K][GB_N + 1];
   const int tid = threadIdx.x, tr = tid & 15, tc = tid >> 4;
   for (int64_t o = blockIdx.x; o < count; o += gridDim.x) {
     const OpGemm op = ops[o];
     const int m = dimv(op.m, B.ranks), k = dimv(op.k, B.ranks), c = dimv(op.c, B.ranks);
     if (m <= 0 || c <= 0) continue;
+    if (B.flops && threadIdx.x == 0)
+      atomicAdd(B.flops + OP_GEMM, op.B.buf < 0 ? (double)m * c : 2.0 * m * (double)k * c);
     double* Y = vptr(B, op.Y);
     const double* A = vptr(B, op.A);
     if (op.B.buf < 0) {  // Y = beta Y + alpha A
@@ -405,28 +351,28 @@ __global__ void __launch_bounds__(256) k_gemm(const OpGemm* ops, int64_t count, 
     const double* Bm = vptr(B, op.B);
     for (int ti = 0; ti < m; ti += GB_M) {
       for (int tj = 0; tj < c; tj += GB_N) {
-        double acc[4][2];
+        T acc[4][2];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) acc[a][0] = acc[a][1] = 0.0;
+        for (int a = 0; a < 4; ++a) acc[a][0] = acc[a][1] = T(0);
         for (int kk = 0; kk < k; kk += GB_K) {
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             const int e = tid + q * 256;
             const int kq = e / GB_M, iq = e % GB_M;
             const int gi = ti + iq, gk = kk + kq;
-            As[kq][iq] = (gi < m && gk < k) ? A[(int64_t)gi * op.A.rs + (int64_t)gk * op.A.cs] : 0.0;
+            As[kq][iq] = (gi < m && gk < k) ? (T)A[(int64_t)gi * op.A.rs + (int64_t)gk * op.A.cs] : T(0);
           }
 #pragma unroll
           for (int q = 0; q < 2; ++q) {
             const int e = tid + q * 256;
             const int kq = e / GB_N, jq = e % GB_N;
             const int gj = tj + jq, gk = kk + kq;
-            Bs[kq][jq] = (gj < c && gk < k) ? Bm[(int64_t)gk * op.B.rs + (int64_t)gj * op.B.cs] : 0.0;
+            Bs[kq][jq] = (gj < c && gk < k) ? (T)Bm[(int64_t)gk * op.B.rs + (int64_t)gj * op.B.cs] : T(0);
           }
           __syncthreads();
 #pragma unroll
           for (int q = 0; q < GB_K; ++q) {
-            double a[4], b[2];
+            T a[4], b[2];
 #pragma unroll
             for (int x = 0; x < 4; ++x) a[x] = As[q][tr * 4 + x];
             b[0] = Bs[q][tc * 2];
@@ -446,311 +392,12 @@ __global__ void __launch_bounds__(256) k_gemm(const OpGemm* ops, int64_t count, 
             const int gi = ti + tr * 4 + x, gj = tj + tc * 2 + y;
             if (gi < m && gj < c) {
               double* yp = Y + (int64_t)gi * op.Y.rs + (int64_t)gj * op.Y.cs;
-              const double v = op.alpha * acc[x][y];
+              const double v = op.alpha * (double)acc[x][y];
               *yp = op.beta ? *yp + v : v;
             }
           }
       }
     }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// TRUNC: target := trunc(target + sum of terms) (Remark A.1), in batches of
-// at most TR_KB new columns: acc := trunc(acc + batch).
-//
-// For K = rank(acc) + batch columns with concatenated factors Ucat (m x K),
-// Vcat (n x K):
-//   1. R_u, R_v: R factors of Ucat and Vcat by Householder QR streamed over
-//      row chunks of TR_CH rows ([R; chunk] -> R), Q never formed;
-//   2. M = R_u R_v^T (K x K), one-sided Jacobi: M J = W, sigma_j = |W_j|;
-//   3. keep sigma_j > eps sigma_max (sorted), k columns;
-//   4. U_new = Ucat R_v^T J_k S_k^-1/2,  V_new = Vcat R_u^T W_k S_k^-3/2,
-//      so that U_new V_new^T = Q_u X_k S_k Y_k^T Q_v^T (the truncated SVD)
-//      and both factors carry S_k^1/2.
-// ---------------------------------------------------------------------------
-constexpr int TR_KB = 64;
-constexpr int TR_KT = 192;  // rank capacity (<= 64) + one batch (<= 64 columns, or one dense term <= 128)
-constexpr int TR_CH = 64;
-constexpr int TR_THREADS = 256;
-constexpr int TR_OUT_LD = 65;
-constexpr int64_t TR_SCRATCH = 4LL * TR_KT * TR_KT + 2LL * TR_KT * 64 + 4LL * TR_KT;
-
-size_t trunc_smem_bytes() {
-  const size_t a = (size_t)TR_CH * TR_KT, b = (size_t)TR_THREADS * TR_OUT_LD;
-  return (a > b ? a : b) * sizeof(double);
-}
-int64_t trunc_scratch_doubles() { return TR_SCRATCH; }
-
-struct TrCat {
-  // column map of the current concatenation
-  int kacc;           // leading columns from the target itself
-  int nt;             // terms in the batch
-  const TermD* terms; // batch terms
-  int col0[65];       // first concatenated column of each batch term (col0[nt] = K)
-};
-
-// value of column `col` of Ucat (side 0) or Vcat (side 1) at row `row`
-__device__ __forceinline__ double cat_value(const Bases& B, const OpTrunc& op, const TrCat& cat, int side,
-                                            int row, int col) {
-  if (col < cat.kacc) {
-    return side == 0 ? B.buf[op.U.buf][op.U.off + row + (int64_t)col * op.m]
-                     : B.buf[op.V.buf][op.V.off + row + (int64_t)col * op.n];
-  }
-  int t = 0;
-  while (col >= cat.col0[t + 1]) ++t;
-  const TermD& d = cat.terms[t];
-  const int lc = col - cat.col0[t];
-  if (side == 0) {
-    const int ii = row - d.roff;
-    if (ii < 0 || ii >= d.urows) return 0.0;
-    if (d.flags & 1) return ii == lc ? d.alpha : 0.0;
-    return d.alpha * B.buf[d.U.buf][d.U.off + (int64_t)ii * d.U.rs + (int64_t)lc * d.U.cs];
-  } else {
-    const int jj = row - d.coff;
-    if (jj < 0 || jj >= d.vrows) return 0.0;
-    if (d.flags & 2) return jj == lc ? 1.0 : 0.0;
-    return B.buf[d.V.buf][d.V.off + (int64_t)jj * d.V.rs + (int64_t)lc * d.V.cs];
-  }
-}
-
-// R factor (K x K, ld TR_KT) of the M x K concatenation of one side.
-__device__ void tr_qr(const Bases& B, const OpTrunc& op, const TrCat& cat, int side, int M, int K, double* R,
-                      double* sC, double* sTau) {
-  const int tid = threadIdx.x;
-  for (int e = tid; e < K * K; e += blockDim.x) R[(e % K) + (int64_t)(e / K) * TR_KT] = 0.0;
-  __syncthreads();
-  for (int r0 = 0; r0 < M; r0 += TR_CH) {
-    const int rows = min(TR_CH, M - r0);
-    for (int e = tid; e < rows * K; e += blockDim.x) {
-      const int i = e % rows, c = e / rows;
-      sC[i + c * TR_CH] = cat_value(B, op, cat, side, r0 + i, c);
-    }
-    __syncthreads();
-    for (int j = 0; j < K; ++j) {
-      if (tid == 0) {
-        const double alpha = R[j + (int64_t)j * TR_KT];
-        double xn = 0.0;
-        for (int i = 0; i < rows; ++i) xn += sC[i + j * TR_CH] * sC[i + j * TR_CH];
-        double tau = 0.0;
-        if (xn > 0.0) {
-          const double beta = -copysign(sqrt(alpha * alpha + xn), alpha);
-          tau = (beta - alpha) / beta;
-          const double sc = 1.0 / (alpha - beta);
-          for (int i = 0; i < rows; ++i) sC[i + j * TR_CH] *= sc;
-          R[j + (int64_t)j * TR_KT] = beta;
-        }
-        sTau[0] = tau;
-      }
-      __syncthreads();
-      const double tau = sTau[0];
-      if (tau != 0.0) {
-        for (int l = j + 1 + tid; l < K; l += blockDim.x) {
-          double w = R[j + (int64_t)l * TR_KT];
-          for (int i = 0; i < rows; ++i) w += sC[i + j * TR_CH] * sC[i + l * TR_CH];
-          w *= tau;
-          R[j + (int64_t)l * TR_KT] -= w;
-          for (int i = 0; i < rows; ++i) sC[i + l * TR_CH] -= w * sC[i + j * TR_CH];
-        }
-      }
-      __syncthreads();
-    }
-  }
-}
-
-__global__ void __launch_bounds__(TR_THREADS) k_trunc(const OpTrunc* ops, int64_t count, const TermD* terms,
-                                                       Bases B) {
-  extern __shared__ double sm[];
-  __shared__ TrCat cat;
-  __shared__ double sTau[2];
-  __shared__ double red[33];
-  __shared__ int s_rot, s_k, s_order[TR_KT];
-  __shared__ double s_sv[TR_KT];
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
-  double* scr = B.scratch + (int64_t)blockIdx.x * TR_SCRATCH;
-  double* Ru = scr;
-  double* Rv = Ru + TR_KT * TR_KT;
-  double* M = Rv + TR_KT * TR_KT;
-  double* J = M + TR_KT * TR_KT;
-  double* Cu = J + TR_KT * TR_KT;
-  double* Cv = Cu + TR_KT * 64;
-  for (int64_t o = blockIdx.x; o < count; o += gridDim.x) {
-    const OpTrunc op = ops[o];
-    const TermD* tl = terms + op.term0;
-    int kacc = op.keep ? B.ranks[op.slot] : 0;
-    int t0 = 0;
-    bool first = true;
-    while (first || t0 < op.nterms) {
-      first = false;
-      // batch [t0, t1)
-      int t1 = t0, kb = 0;
-      while (t1 < op.nterms) {
-        const int kt = (tl[t1].flags & 1) ? tl[t1].urows : (tl[t1].flags & 2) ? tl[t1].vrows
-                                                                              : dimv(tl[t1].k, B.ranks);
-        if (kb != 0 && kb + kt > TR_KB) break;
-        if (t1 - t0 >= 64) break;
-        kb += kt;
-        ++t1;
-      }
-      const int K = kacc + kb;
-      __syncthreads();
-      if (tid == 0) {
-        cat.kacc = kacc;
-        cat.nt = t1 - t0;
-        cat.terms = tl + t0;
-        int c = kacc;
-        for (int t = t0; t < t1; ++t) {
-          cat.col0[t - t0] = c;
-          c += (tl[t].flags & 1) ? tl[t].urows : (tl[t].flags & 2) ? tl[t].vrows : dimv(tl[t].k, B.ranks);
-        }
-        cat.col0[t1 - t0] = c;
-      }
-      __syncthreads();
-      t0 = t1;
-      if (K == 0) {
-        kacc = 0;
-        continue;
-      }
-      if (K > TR_KT) {
-        if (tid == 0) record_error(B.status, DEV_RANK, K);
-        kacc = 0;
-        break;
-      }
-      tr_qr(B, op, cat, 0, op.m, K, Ru, sm, sTau);
-      tr_qr(B, op, cat, 1, op.n, K, Rv, sm, sTau);
-      // M = Ru Rv^T ; J = I
-      for (int e = tid; e < K * K; e += blockDim.x) {
-        const int i = e % K, j = e / K;
-        double s = 0.0;
-        for (int c = max(i, j); c < K; ++c) s += Ru[i + (int64_t)c * TR_KT] * Rv[j + (int64_t)c * TR_KT];
-        M[i + (int64_t)j * TR_KT] = s;
-        J[i + (int64_t)j * TR_KT] = (i == j) ? 1.0 : 0.0;
-      }
-      __syncthreads();
-      // one-sided Jacobi, round-robin pairs
-      double fro2 = 0.0;
-      for (int e = tid; e < K * K; e += blockDim.x) {
-        const double v = M[(e % K) + (int64_t)(e / K) * TR_KT];
-        fro2 += v * v;
-      }
-      fro2 = block_sum(fro2, red);
-      const double tiny = 1e-34 * fro2;
-      const int Kp = K + (K & 1);
-      for (int sweep = 0; sweep < 80; ++sweep) {
-        if (tid == 0) s_rot = 0;
-        __syncthreads();
-        for (int step = 0; step < Kp - 1; ++step) {
-          for (int q = w; q < Kp / 2; q += nw) {
-            const int pa = q, pb = Kp - 1 - q;
-            int a = pa == 0 ? 0 : 1 + (pa - 1 + step) % (Kp - 1);
-            int b = pb == 0 ? 0 : 1 + (pb - 1 + step) % (Kp - 1);
-            if (a > b) {
-              const int t = a;
-              a = b;
-              b = t;
-            }
-            if (b >= K) continue;
-            double al = 0.0, be = 0.0, ga = 0.0;
-            for (int r = lane; r < K; r += 32) {
-              const double x = M[r + (int64_t)a * TR_KT], y = M[r + (int64_t)b * TR_KT];
-              al += x * x;
-              be += y * y;
-              ga += x * y;
-            }
-            al = warp_sum(al);
-            be = warp_sum(be);
-            ga = warp_sum(ga);
-            if (al <= tiny && be <= tiny) continue;
-            if (ga == 0.0 || fabs(ga) <= 1e-15 * sqrt(al * be)) continue;
-            const double zeta = (be - al) / (2.0 * ga);
-            const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-            const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
-            for (int r = lane; r < K; r += 32) {
-              const double x = M[r + (int64_t)a * TR_KT], y = M[r + (int64_t)b * TR_KT];
-              M[r + (int64_t)a * TR_KT] = cs * x - sn * y;
-              M[r + (int64_t)b * TR_KT] = sn * x + cs * y;
-              const double jx = J[r + (int64_t)a * TR_KT], jy = J[r + (int64_t)b * TR_KT];
-              J[r + (int64_t)a * TR_KT] = cs * jx - sn * jy;
-              J[r + (int64_t)b * TR_KT] = sn * jx + cs * jy;
-            }
-            if (lane == 0) s_rot = 1;
-          }
-          __syncthreads();
-        }
-        if (!s_rot) break;
-        __syncthreads();
-      }
-      // singular values, order (ties: smaller index first), truncation rank
-      for (int j = tid; j < K; j += blockDim.x) {
-        double s = 0.0;
-        for (int r = 0; r < K; ++r) s += M[r + (int64_t)j * TR_KT] * M[r + (int64_t)j * TR_KT];
-        s_sv[j] = sqrt(s);
-      }
-      __syncthreads();
-      for (int j = tid; j < K; j += blockDim.x) {
-        int rank = 0;
-        for (int i = 0; i < K; ++i) rank += (s_sv[i] > s_sv[j]) || (s_sv[i] == s_sv[j] && i < j);
-        s_order[rank] = j;
-      }
-      __syncthreads();
-      if (tid == 0) {
-        const double smax = s_sv[s_order[0]];
-        int k = 0;
-        if (smax > 0.0)
-          while (k < K && s_sv[s_order[k]] > op.eps * smax) ++k;
-        if (!(smax == smax)) {
-          record_error(B.status, DEV_BAD, 1);
-          k = 0;
-        }
-        if (k > op.kcap) {
-          record_error(B.status, DEV_RANK, k);
-          k = op.kcap;
-        }
-        s_k = k;
-      }
-      __syncthreads();
-      const int k = s_k;
-      // coefficients
-      for (int e = tid; e < K * k; e += blockDim.x) {
-        const int col = e % K, c = e / K;
-        const int j = s_order[c];
-        const double sv = s_sv[j], isq = 1.0 / sqrt(sv);
-        double a = 0.0, b = 0.0;
-        for (int p = 0; p <= col; ++p) {
-          a += Rv[p + (int64_t)col * TR_KT] * J[p + (int64_t)j * TR_KT];
-          b += Ru[p + (int64_t)col * TR_KT] * M[p + (int64_t)j * TR_KT];
-        }
-        Cu[col + (int64_t)c * TR_KT] = a * isq;
-        Cv[col + (int64_t)c * TR_KT] = b * isq / sv;
-      }
-      __syncthreads();
-      // apply, row-local and in place
-      for (int side = 0; side < 2; ++side) {
-        const int rows = side == 0 ? op.m : op.n;
-        const double* C = side == 0 ? Cu : Cv;
-        double* out = side == 0 ? B.buf[op.U.buf] + op.U.off : B.buf[op.V.buf] + op.V.off;
-        double* so = sm + tid * TR_OUT_LD;
-        for (int r0 = 0; r0 < rows; r0 += blockDim.x) {
-          const int r = r0 + tid;
-          if (r < rows) {
-            for (int c = 0; c < k; ++c) so[c] = 0.0;
-            for (int col = 0; col < K; ++col) {
-              const double v = cat_value(B, op, cat, side, r, col);
-              if (v != 0.0)
-                for (int c = 0; c < k; ++c) so[c] += v * C[col + (int64_t)c * TR_KT];
-            }
-          }
-          __syncthreads();
-          if (r < rows)
-            for (int c = 0; c < k; ++c) out[r + (int64_t)c * rows] = so[c];
-          __syncthreads();
-        }
-      }
-      kacc = k;
-      __syncthreads();
-    }
-    if (tid == 0) B.ranks[op.slot] = kacc;
-    __syncthreads();
   }
 }
 
@@ -825,12 +472,14 @@ void launch_dense_asm(const DenseAsm* d, int64_t count, double* arena, const dou
   k_dense_asm<<<grid_for(count, 152 * 16), 256, 0, st>>>(d, count, arena, px, py, mp);
 }
 void launch_aca(const LrAsm* d, int64_t count, double* arena, const double* px, const double* py,
-                const MaternDev& mp, double eps, int* ranks, cudaStream_t st) {
+                const MaternDev& mp, double eps, int* ranks, bool mixed, cudaStream_t st) {
   if (count <= 0) return;
-  k_aca<<<grid_for(count, 152 * 8), ACA_THREADS, 0, st>>>(d, count, arena, px, py, mp, eps, ranks);
+  if (mixed)
+    k_aca<float><<<grid_for(count, 152 * 8), ACA_THREADS, 0, st>>>(d, count, arena, px, py, mp, eps, ranks);
+  else
+    k_aca<double><<<grid_for(count, 152 * 8), ACA_THREADS, 0, st>>>(d, count, arena, px, py, mp, eps, ranks);
 }
 
-int max_trunc_ctas() { return 152 * 2; }
 
 void launch_ops(int type, const void* ops, int64_t count, const TermD* terms, const Bases& B, int max_dense,
                 cudaStream_t st) {
@@ -845,11 +494,16 @@ void launch_ops(int type, const void* ops, int64_t count, const TermD* terms, co
           (const OpTrsm*)ops, count, B);
       break;
     case OP_GEMM:
-      k_gemm<<<grid_for(count, 152 * 16), 256, 0, st>>>((const OpGemm*)ops, count, B);
+      if (B.mixed)
+        k_gemm<float><<<grid_for(count, 152 * 16), 256, 0, st>>>((const OpGemm*)ops, count, B);
+      else
+        k_gemm<double><<<grid_for(count, 152 * 16), 256, 0, st>>>((const OpGemm*)ops, count, B);
       break;
     case OP_TRUNC:
-      k_trunc<<<grid_for(count, max_trunc_ctas()), TR_THREADS, trunc_smem_bytes(), st>>>((const OpTrunc*)ops,
-                                                                                         count, terms, B);
+      launch_trunc((const OpTrunc*)ops, count, terms, B, false, st);
+      break;
+    case OP_TRUNC_BIG:
+      launch_trunc((const OpTrunc*)ops, count, terms, B, true, st);
       break;
   }
 }
@@ -883,9 +537,8 @@ int configure_kernels(int max_dense) {
   const size_t need = (size_t)max_dense * max_dense * sizeof(double);
   cudaError_t e1 = cudaFuncSetAttribute(k_potrf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
   cudaError_t e2 = cudaFuncSetAttribute(k_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
-  cudaError_t e3 =
-      cudaFuncSetAttribute(k_trunc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trunc_smem_bytes());
-  return (e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess) ? 0 : -1;
+  const int e3 = configure_trunc();
+  return (e1 == cudaSuccess && e2 == cudaSuccess && e3 == 0) ? 0 : -1;
 }
 
 }  // namespace hlc

@@ -6,15 +6,17 @@
 
 namespace hlc {
 
-size_t trunc_smem_bytes();
 int64_t trunc_scratch_doubles();
 int max_trunc_ctas();
+int configure_trunc();
+void launch_trunc(const OpTrunc* ops, int64_t count, const TermD* terms, const Bases& B, bool big,
+                  cudaStream_t st);
 int configure_kernels(int max_dense);
 
 void launch_dense_asm(const DenseAsm* d, int64_t count, double* arena, const double* px, const double* py,
                       const MaternDev& mp, cudaStream_t st);
 void launch_aca(const LrAsm* d, int64_t count, double* arena, const double* px, const double* py,
-                const MaternDev& mp, double eps, int* ranks, cudaStream_t st);
+                const MaternDev& mp, double eps, int* ranks, bool mixed, cudaStream_t st);
 void launch_ops(int type, const void* ops, int64_t count, const TermD* terms, const Bases& B, int max_dense,
                 cudaStream_t st);
 void launch_gather(const double* src, const int32_t* perm, double* dst, int64_t n, cudaStream_t st);
@@ -25,5 +27,11 @@ void launch_sub(const double* x, const double* y, double* z, int64_t n, cudaStre
 void launch_dot(const double* x, const double* y, int64_t n, double* part, double* out, cudaStream_t st);
 void launch_logdet(const int64_t* offs, const int32_t* dims, int64_t count, const double* arena, double* part,
                    double* out, cudaStream_t st);
+
+// Device build of the cluster tree and block-cluster tree (tree.cu); returns
+// 0 or -1 on a CUDA failure.
+int device_tree_build(const double* d_xy, int64_t n, int leaf, double eta, cudaStream_t st,
+                      std::vector<int32_t>& perm, std::vector<Cluster>& clusters, std::vector<Block>& blocks,
+                      int* depth);
 
 }  // namespace hlc

@@ -7,8 +7,10 @@ library and fails loudly when it has not been built.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 import os
+import weakref
 
 import numpy as np
 
@@ -42,7 +44,7 @@ class hlc_result(ctypes.Structure):
                 ("quad_factor", ctypes.c_double), ("refine_iters", ctypes.c_int),
                 ("rel_residual", ctypes.c_double), ("bytes_C", ctypes.c_size_t), ("bytes_L", ctypes.c_size_t),
                 ("max_rank_C", ctypes.c_int), ("max_rank_L", ctypes.c_int), ("ms_assemble", ctypes.c_double),
-                ("ms_factor", ctypes.c_double), ("ms_solve", ctypes.c_double)]
+                ("ms_factor", ctypes.c_double), ("ms_solve", ctypes.c_double), ("ms_total", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -78,6 +80,9 @@ _SIGS = {
     "hlc_hmat_ranks": (ctypes.c_int, [_vp, _vp, _vp]),
     "hlc_hmat_free": (None, [_vp]),
     "hlc_loglik": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(hlc_theta), _vp, ctypes.POINTER(hlc_result)]),
+    "hlc_ctx_stream": (ctypes.c_int, [_vp, ctypes.POINTER(_vp)]),
+    "hlc_ctx_set_profiling": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "hlc_ctx_counters": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
     "hlc_serve_start": (ctypes.c_int, [_vp, ctypes.c_size_t, ctypes.c_int]),
     "hlc_serve_submit": (ctypes.c_int, [_vp, _vp, _vp, _i64, ctypes.POINTER(hlc_theta), ctypes.POINTER(hlc_params),
                                         ctypes.POINTER(ctypes.c_uint64)]),
@@ -95,6 +100,22 @@ def lib():
     return _lib
 
 
+# Handles still alive at interpreter exit are released here, in dependency
+# order, while the CUDA runtime is still loaded (object finalisers may run
+# after it has been torn down).
+_LIVE = {"trees": weakref.WeakSet(), "mats": weakref.WeakSet(), "ctxs": weakref.WeakSet()}
+
+
+@atexit.register
+def _release_all():
+    for kind, meth in (("mats", "free"), ("trees", "free"), ("ctxs", "close")):
+        for obj in list(_LIVE[kind]):
+            try:
+                getattr(obj, meth)()
+            except Exception:
+                pass
+
+
 def _ptr(a):
     if a is None:
         return None
@@ -108,7 +129,7 @@ def _check(st, what):
         raise HlcError(st, what)
 
 
-def params(leaf=64, eta=2.0, eps=1e-6, precision=HLC_FP64, refine_tol=1e-12, refine_maxit=30, kmax=64):
+def params(leaf=64, eta=2.0, eps=1e-6, precision=HLC_FP64, refine_tol=1e-12, refine_maxit=100, kmax=64):
     p = hlc_params()
     hlc_default_params(ctypes.byref(p))
     p.leaf, p.eta, p.eps, p.precision = int(leaf), float(eta), float(eps), int(precision)
@@ -127,6 +148,7 @@ class Context:
         h = _vp()
         _check(hlc_create(ctypes.byref(h), int(device)), "hlc_create")
         self.h = h
+        _LIVE["ctxs"].add(self)
 
     def close(self):
         if getattr(self, "h", None):
@@ -139,10 +161,55 @@ class Context:
     def build_tree(self, xy, **kw):
         return Tree(self, xy, **kw)
 
+    def stream(self):
+        """The context's cudaStream_t as an integer handle."""
+        p = _vp()
+        _check(hlc_ctx_stream(self.h, ctypes.byref(p)), "hlc_ctx_stream")
+        return p.value or 0
+
+    def set_profiling(self, on=True):
+        _check(hlc_ctx_set_profiling(self.h, int(bool(on))), "hlc_ctx_set_profiling")
+
+    OPS = ("potrf", "trsm", "gemm", "trunc", "trunc_cluster")
+
+    # ---- serving -------------------------------------------------------
+    def serve_start(self, hbm_budget_bytes, max_slots):
+        _check(hlc_serve_start(self.h, int(hbm_budget_bytes), int(max_slots)), "hlc_serve_start")
+
+    def serve_submit(self, xy, z, th, **kw):
+        xy = np.ascontiguousarray(xy, dtype=np.float64)
+        z = np.ascontiguousarray(z, dtype=np.float64)
+        p = params(**kw)
+        rid = ctypes.c_uint64()
+        _check(hlc_serve_submit(self.h, _ptr(xy), _ptr(z), xy.shape[0], ctypes.byref(th), ctypes.byref(p),
+                                ctypes.byref(rid)), "hlc_serve_submit")
+        return rid.value
+
+    def serve_poll(self, rid):
+        """None while pending, else the result dict (raises on a failed request)."""
+        r = hlc_result()
+        st = hlc_serve_poll(self.h, ctypes.c_uint64(rid), ctypes.byref(r))
+        if st == HLC_PENDING:
+            return None
+        _check(st, "hlc_serve_poll")
+        return r.as_dict()
+
+    def serve_stop(self):
+        _check(hlc_serve_stop(self.h), "hlc_serve_stop")
+
+    def counters(self, reset=False):
+        a = np.zeros(17)
+        _check(hlc_ctx_counters(self.h, int(bool(reset)), _ptr(a)), "hlc_ctx_counters")
+        out = {"launches": int(a[0])}
+        for i, name in enumerate(self.OPS):
+            out[name] = {"launches": int(a[1 + 3 * i]), "ms": float(a[2 + 3 * i]), "flops": float(a[3 + 3 * i])}
+        return out
+
 
 class HMat:
     def __init__(self, ctx, tree, h):
         self.ctx, self.tree, self.h = ctx, tree, h
+        _LIVE["mats"].add(self)
 
     def free(self):
         if getattr(self, "h", None):
@@ -175,7 +242,7 @@ class Tree:
     """hlc_build_tree and the calls on a tree."""
 
     def __init__(self, ctx, xy, leaf=64, eta=2.0, eps=1e-6, precision=HLC_FP64, refine_tol=1e-12,
-                 refine_maxit=30, kmax=64):
+                 refine_maxit=100, kmax=64):
         self.ctx = ctx
         if not hasattr(xy, "data_ptr"):
             xy = np.ascontiguousarray(xy, dtype=np.float64)
@@ -185,6 +252,7 @@ class Tree:
         h = _vp()
         _check(hlc_build_tree(ctx.h, _ptr(xy), self.n, ctypes.byref(self.p), ctypes.byref(h)), "hlc_build_tree")
         self.h = h
+        _LIVE["trees"].add(self)
         info = self.info()
         self.nleaves = info["dense"] + info["lowrank"]
 
