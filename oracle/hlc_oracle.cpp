@@ -152,16 +152,19 @@ void householder_qr(const Mat& A, Mat& Q, Mat& R) {
 
 // One-sided (Hestenes) Jacobi SVD of B (p x q): B = X diag(S) Y^T with the
 // singular values sorted in decreasing order; X is p x r, Y is q x r with
-// r = min(p, q).  Rotations run on the narrower side (B or B^T).  Pairs of
-// columns that are both below 1e-17 |B|_F carry no information above any
-// truncation threshold and are left alone.
+// r = min(p, q).  Rotations run on the narrower side (B or B^T).  A pair of
+// columns is rotated while |gamma| > max(p, 16) u sqrt(alpha beta)
+// (u = 2^-53, the usual one-sided Jacobi criterion); pairs of columns both
+// below 1e-13 |B|_F are at rounding level, carry nothing above any truncation
+// threshold and are left alone.
 void jacobi_svd_cols(Mat& B, Mat& Y) {
   const long p = B.m, q = B.n;
   Y = Mat(q, q);
   for (long i = 0; i < q; ++i) Y(i, i) = 1.0;
   double fro2 = 0.0;
   for (double v : B.a) fro2 += v * v;
-  const double tiny = 1e-34 * fro2;
+  const double tiny = 1e-26 * fro2;
+  const double rtol = (double)std::max<long>(p, 16) * 1.1102230246251565e-16;
   for (int sweep = 0; sweep < 80; ++sweep) {
     bool rotated = false;
     for (long i = 0; i < q - 1; ++i) {
@@ -173,7 +176,7 @@ void jacobi_svd_cols(Mat& B, Mat& Y) {
           g += B(k, i) * B(k, j);
         }
         if (a <= tiny && b <= tiny) continue;
-        if (g == 0.0 || std::fabs(g) <= 1e-15 * std::sqrt(a * b)) continue;
+        if (g == 0.0 || std::fabs(g) <= rtol * std::sqrt(a * b)) continue;
         rotated = true;
         const double zeta = (b - a) / (2.0 * g);
         const double t = (zeta >= 0.0 ? 1.0 : -1.0) /
