@@ -153,10 +153,11 @@ void householder_qr(const Mat& A, Mat& Q, Mat& R) {
 // One-sided (Hestenes) Jacobi SVD of B (p x q): B = X diag(S) Y^T with the
 // singular values sorted in decreasing order; X is p x r, Y is q x r with
 // r = min(p, q).  Rotations run on the narrower side (B or B^T).  A pair of
-// columns is rotated while |gamma| > max(p, 16) u sqrt(alpha beta)
-// (u = 2^-53, the usual one-sided Jacobi criterion); pairs of columns both
-// below 1e-13 |B|_F are at rounding level, carry nothing above any truncation
-// threshold and are left alone.
+// columns is rotated while |gamma| > max(p, 16) 1e-14 sqrt(alpha beta): the
+// columns end orthogonal to ~1e-13, far below any truncation threshold,
+// without chasing the rounding noise of the length-p dot products; pairs of
+// columns both below 1e-13 |B|_F are at rounding level, carry nothing above
+// any truncation threshold and are left alone.
 void jacobi_svd_cols(Mat& B, Mat& Y) {
   const long p = B.m, q = B.n;
   Y = Mat(q, q);
@@ -164,7 +165,7 @@ void jacobi_svd_cols(Mat& B, Mat& Y) {
   double fro2 = 0.0;
   for (double v : B.a) fro2 += v * v;
   const double tiny = 1e-26 * fro2;
-  const double rtol = (double)std::max<long>(p, 16) * 1.1102230246251565e-16;
+  const double rtol = (double)std::max<long>(p, 16) * 1e-14;
   for (int sweep = 0; sweep < 80; ++sweep) {
     bool rotated = false;
     for (long i = 0; i < q - 1; ++i) {
