@@ -64,7 +64,7 @@ def lib():
         L.orc_h_leaf_blocks.argtypes = [ctypes.c_void_p, _lp]
         L.orc_h_leaf_blocks.restype = ctypes.c_long
         L.orc_h_assemble.argtypes = [ctypes.c_void_p] + [ctypes.c_double] * 5 + [ctypes.c_long]
-        L.orc_h_cholesky.argtypes = [ctypes.c_void_p, ctypes.c_double]
+        L.orc_h_cholesky.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int]
         L.orc_h_cholesky.restype = ctypes.c_long
         L.orc_h_stats.argtypes = [ctypes.c_void_p, _lp]
         L.orc_h_ranks.argtypes = [ctypes.c_void_p, ctypes.c_int, _ip]
@@ -212,8 +212,8 @@ class HOracle:
             raise ValueError("orc_h_assemble failed")
         self.eps = eps
 
-    def cholesky(self, eps=None):
-        st = lib().orc_h_cholesky(self.h, float(self.eps if eps is None else eps))
+    def cholesky(self, eps=None, accumulate=False):
+        st = lib().orc_h_cholesky(self.h, float(self.eps if eps is None else eps), int(bool(accumulate)))
         if st == -2:
             raise np.linalg.LinAlgError("H-Cholesky: not positive definite")
         if st != 0:
@@ -264,11 +264,11 @@ class HOracle:
         return Uk, Vk
 
 
-def h_loglik(xy, z, sigma2, ell, nu, nugget, eps, leaf=32, eta=2.0, tol=1e-12, maxit=100):
+def h_loglik(xy, z, sigma2, ell, nu, nugget, eps, leaf=32, eta=2.0, tol=1e-12, maxit=100, accumulate=False):
     """One oracle evaluation: tree, assembly, H-Cholesky, eq. (2) + preconditioned CG."""
     H = HOracle(xy, leaf=leaf, eta=eta)
     H.assemble(sigma2, ell, nu, nugget, eps)
-    H.cholesky(eps)
+    H.cholesky(eps, accumulate=accumulate)
     r = H.loglik(z, tol=tol, maxit=maxit)
     r.update(H.stats())
     return r

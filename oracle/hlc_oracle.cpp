@@ -1333,13 +1333,15 @@ int orc_h_assemble(void* h, double sigma2, double ell, double nu, double nugget,
 }
 
 // H-Cholesky of the assembled matrix (copy, then factor in place).
-long orc_h_cholesky(void* h, double eps) {
+// accumulate = 1: updates of a low-rank block wait and are truncated together
+// right before the block is next used; 0: every update is truncated at once.
+long orc_h_cholesky(void* h, double eps, int accumulate) {
   HTree* T = static_cast<HTree*>(h);
   if (!T->assembled) return -3;
   T->L = T->C;
   std::vector<std::vector<Term>> pending(T->L.size());
   HCtx H{T, &T->L, eps};
-  H.pending = &pending;
+  H.pending = accumulate ? &pending : nullptr;
 #pragma omp parallel
 #pragma omp single
   chol(H, 0);
