@@ -175,7 +175,9 @@ int hlc_ctx_set_profiling(hlc_ctx* ctx, int on);
  * out[0] kernel launches of the library,
  * out[1 + 3*t .. 3 + 3*t] for op type t in {0 potrf, 1 trsm, 2 gemm,
  *   3 truncation (one CTA), 4 truncation (cluster)}: launches, device ms
- *   (profiling on), algorithmic flops.  17 doubles. */
+ *   (profiling on), algorithmic flops,
+ * out[16] launches of the persistent solve kernel (one per triangular solve
+ *   or matvec; their TRSM/GEMM ops are not counted per type).  17 doubles. */
 int hlc_ctx_counters(hlc_ctx* ctx, int reset, double* out);
 
 /* ---- serving: continuous batching of likelihood requests ------------------ */

@@ -34,9 +34,13 @@ struct hlc_ctx {
   hlc::Serve* serve = nullptr;
   // measurement
   double* d_flops = nullptr;  // NOPTYPES algorithmic flop counters
+  unsigned long long* d_phase = nullptr;  // truncation phase cycles (HLC_PHASES=1)
+  GridBar* d_gridbar = nullptr;           // barrier state of the persistent solve kernel
+  bool persistent = true;                 // off in serve slots (several contexts share the SMs)
   bool profiling = false;
   double launches = 0;
   double op_launches[NOPTYPES] = {};
+  double persistent_launches = 0;
   double op_ms[NOPTYPES] = {};
   std::vector<cudaEvent_t> evpool;
   struct Pending {
@@ -111,9 +115,33 @@ int upload(T** d, const std::vector<T>& h) {
   return HLC_OK;
 }
 
+// Wave table of a plan made of TRSM and GEMM ops only (solves, matvec).
+void build_waves(Plan& P) {
+  P.waves.clear();
+  for (const Launch& L : P.launches)
+    if (L.type != OP_TRSM && L.type != OP_GEMM) return;
+  int32_t cur = -1;
+  for (const Launch& L : P.launches) {
+    if (L.wave != cur) {
+      P.waves.push_back(WaveRange{0, 0, 0, 0});
+      cur = L.wave;
+    }
+    WaveRange& w = P.waves.back();
+    if (L.type == OP_TRSM) {
+      w.trsm0 = L.first;
+      w.ntrsm = L.count;
+    } else {
+      w.gemm0 = L.first;
+      w.ngemm = L.count;
+    }
+  }
+}
+
 int upload_plan(Plan& P) {
   int st;
   P.checked = true;
+  build_waves(P);
+  if ((st = upload(&P.d_waves, P.waves))) return st;
   if ((st = upload(&P.d_gemm, P.gemm))) return st;
   if ((st = upload(&P.d_trsm, P.trsm))) return st;
   if ((st = upload(&P.d_potrf, P.potrf))) return st;
@@ -125,6 +153,8 @@ int upload_plan(Plan& P) {
 void free_plan(Plan& P) {
   if (P.graph) cudaGraphExecDestroy(P.graph);
   P.graph = nullptr;
+  cudaFree(P.d_waves);
+  P.d_waves = nullptr;
   cudaFree(P.d_gemm);
   cudaFree(P.d_trsm);
   cudaFree(P.d_potrf);
@@ -186,8 +216,23 @@ void run_plan_launches(hlc_tree* t, const Plan& P, const Bases& B, cudaStream_t 
 // Run a plan: replayed from a CUDA graph when possible (the op program is the
 // same for every evaluation on a tree; only the ranks in device memory vary),
 // captured on first use for a given set of base pointers.
+bool persistent_enabled() {
+  static const bool on = !(getenv("HLC_PERSISTENT") && getenv("HLC_PERSISTENT")[0] == '0');
+  return on;
+}
+
 void run_plan(hlc_tree* t, const Plan& P, const Bases& B, cudaStream_t st) {
   hlc_ctx* c = t->ctx;
+  // TRSM/GEMM plans (solves, matvec): one persistent cooperative launch
+  if (P.d_waves && !P.waves.empty() && c->persistent && !c->profiling && !g_prof.on && persistent_enabled()) {
+    const int md = (int)std::max<int64_t>(t->T.max_dense_dim, t->T.leaf);
+    if (launch_waves(P.d_waves, (int)P.waves.size(), P.d_trsm, P.d_gemm, B, c->d_gridbar, md, st) == 0) {
+      c->launches += 1;
+      c->persistent_launches += 1;
+      return;
+    }
+    cudaGetLastError();
+  }
   if (c->profiling || g_prof.on || !graphs_enabled() || P.launches.empty()) {
     run_plan_launches(t, P, B, st, true);
     return;
@@ -273,6 +318,7 @@ Bases make_bases(hlc_tree* t, double* mat_L, double* mat_C, int* ranks, bool mix
   B.status = t->ctx->d_status;
   B.scratch = t->ctx->d_scratch;
   B.flops = t->ctx->d_flops;
+  B.phase = t->ctx->d_phase;
   return B;
 }
 
@@ -287,6 +333,7 @@ int take_status(hlc_ctx* c) {
     case DEV_OK: return HLC_OK;
     case DEV_NOT_SPD: return HLC_ERR_NOT_SPD;
     case DEV_RANK: return HLC_ERR_RANK;
+    case DEV_TIMEOUT: return HLC_ERR_TIMEOUT;
     default: return HLC_ERR_NUMERIC;
   }
 }
@@ -351,7 +398,8 @@ int check_plan(hlc_tree* t, const Plan& P) {
 int build_plans(hlc_tree* t, bool chol, bool solve) {
   try {
     if (chol && !t->chol_ready) {
-      plan_cholesky(t->T, t->chol);
+      const bool acc = getenv("HLC_ACCUMULATE") && getenv("HLC_ACCUMULATE")[0] == '1';
+      plan_cholesky(t->T, t->chol, acc);
       int st = check_plan(t, t->chol);
       if (st) return st;
       st = upload_plan(t->chol);
@@ -447,6 +495,7 @@ void hmat_stats(hlc_tree* t, const hlc_hmat* M, size_t* bytes, int* maxr) {
 // ===========================================================================
 namespace hlc {
 Serve*& serve_of(hlc_ctx* c) { return c->serve; }
+void set_persistent(hlc_ctx* c, bool on) { c->persistent = on; }
 int device_of(hlc_ctx* c) { return c->device; }
 }  // namespace hlc
 
@@ -481,8 +530,10 @@ int hlc_ctx_counters(hlc_ctx* c, int reset, double* out) {
     out[2 + 3 * t] = c->op_ms[t];
     out[3 + 3 * t] = fl[t];
   }
+  out[1 + 3 * NOPTYPES] = c->persistent_launches;
   if (reset) {
     c->launches = 0;
+    c->persistent_launches = 0;
     for (int t = 0; t < NOPTYPES; ++t) c->op_launches[t] = c->op_ms[t] = 0;
     CK(cudaMemset(c->d_flops, 0, NOPTYPES * sizeof(double)));
   }
@@ -535,7 +586,12 @@ int hlc_create(hlc_ctx** out, int device) {
   if (e == cudaSuccess) e = cudaMalloc(&c->d_status, 16);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_flops, NOPTYPES * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(c->d_flops, 0, NOPTYPES * sizeof(double));
+  if (e == cudaSuccess && getenv("HLC_PHASES") && getenv("HLC_PHASES")[0] == '1') {
+    e = cudaMalloc(&c->d_phase, 16 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(c->d_phase, 0, 16 * sizeof(unsigned long long));
+  }
   if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, 16);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_gridbar, sizeof(GridBar));
   if (e == cudaSuccess)
     e = cudaMalloc(&c->d_scratch, (size_t)max_trunc_ctas() * trunc_scratch_doubles() * sizeof(double));
   for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&c->ev[i]);
@@ -567,8 +623,24 @@ void hlc_destroy(hlc_ctx* c) {
   cudaFree(c->d_part);
   cudaFree(c->d_scalar);
   cudaFree(c->d_status);
+  cudaFree(c->d_gridbar);
   cudaFree(c->d_scratch);
   cudaFree(c->d_flops);
+  if (c->d_phase) {
+    unsigned long long ph[16];
+    if (cudaMemcpy(ph, c->d_phase, sizeof(ph), cudaMemcpyDeviceToHost) == cudaSuccess && ph[11]) {
+      static const char* nm[8] = {"", "qr U", "qr V", "core M", "core QRCP", "core QR+Jacobi", "core vectors",
+                                  "apply"};
+      double tot = 0;
+      for (int i = 1; i < 8; ++i) tot += (double)ph[i];
+      fprintf(stderr, "hlc-phases batches %llu  mean K %.1f  mean rank %.1f\n", ph[11], (double)ph[12] / ph[11],
+              (double)ph[10] / ph[11]);
+      for (int i = 1; i < 8; ++i)
+        fprintf(stderr, "hlc-phases %-16s %14.0f cycles (%5.1f %%) %10.1f per batch\n", nm[i], (double)ph[i],
+                100.0 * ph[i] / tot, (double)ph[i] / ph[11]);
+    }
+    cudaFree(c->d_phase);
+  }
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
   for (int i = 0; i < 4; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);

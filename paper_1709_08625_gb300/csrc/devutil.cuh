@@ -29,15 +29,21 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Block-wide sum; all threads get the result.  `red` needs 33 doubles.
-__device__ __forceinline__ double block_sum(double v, double* red) {
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum; all threads get the result.  `red` needs 33 entries.
+template <class T>
+__device__ __forceinline__ T block_sum(T v, T* red) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   v = warp_sum(v);
   __syncthreads();
   if (lane == 0) red[w] = v;
   __syncthreads();
   if (w == 0) {
-    double t = lane < nw ? red[lane] : 0.0;
+    T t = lane < nw ? red[lane] : T(0);
     t = warp_sum(t);
     if (lane == 0) red[32] = t;
   }

@@ -294,6 +294,7 @@ struct TermP {
 };
 const int64_t kTruncBigRows = 4096;   // m + n above which a truncation uses a cluster
 const int64_t kGemmSplitRows = 4096;  // row block of a split product
+const int64_t kGemmSplitK = 2048;     // inner block of a split matrix-vector product
 const int64_t kPendingCols = INT64_MAX;  // no size-forced truncation: flush only on use
 
 struct Planner {
@@ -491,6 +492,33 @@ struct Planner {
   // ---- op emission ----
   void gemm(const PV& Y, const PV& A, const PV& B, Dim m, Dim k, Dim c, double alpha) {
     if (m.n <= 0 || c.n <= 0 || k.n <= 0) return;
+    // matrix-vector products with a long inner dimension: partial products
+    // of inner blocks into disjoint slices of a temporary (one CTA each),
+    // then their sum in a fixed order
+    if (c.slot < 0 && c.n == 1 && k.slot < 0 && k.n > kGemmSplitK) {
+      const int64_t nq = (k.n + kGemmSplitK - 1) / kGemmSplitK, mc = m.n;
+      const int32_t t = new_tmp(mc * nq, 1);
+      const PV Pt = whole(t, mc * nq, 1);
+      for (int64_t q = 0; q < nq; ++q) {
+        const int64_t k0 = q * kGemmSplitK, k1 = std::min<int64_t>(k.n, k0 + kGemmSplitK);
+        gemm(rows(Pt, q * mc, (q + 1) * mc), cols(A, k0, k1), rows(B, k0, k1), m, dim(k1 - k0, NOSLOT), c, 1.0);
+      }
+      OpGemm op;
+      op.Y = mv(Y);
+      op.A = mv(Pt);
+      op.A.cs = mc;  // the slices side by side: element (i, q) at i + q mc
+      op.B = Mv{0, 0, 0, MV_ONES, 0};
+      op.m = m;
+      op.k = dim(nq, NOSLOT);
+      op.c = c;
+      op.alpha = alpha;
+      op.beta = first_write_beta(Y);
+      op.pad = 0;
+      const int32_t w = place({Pt}, {Y});
+      P.gemm.push_back(op);
+      seq.push_back(Ref{OP_GEMM, (int64_t)P.gemm.size() - 1, w});
+      return;
+    }
     // tall products split into independent row blocks (one CTA each)
     if (m.slot < 0 && m.n > kGemmSplitRows) {
       for (int64_t r0 = 0; r0 < m.n; r0 += kGemmSplitRows) {
@@ -519,7 +547,7 @@ struct Planner {
     OpGemm op;
     op.Y = mv(Y);
     op.A = mv(X);
-    op.B = Mv{0, 0, 0, -1, 0};
+    op.B = Mv{0, 0, 0, MV_IDENTITY, 0};
     op.m = m;
     op.k = c;
     op.c = c;
@@ -1115,8 +1143,10 @@ std::string validate_plan(const Plan& P, const int64_t* bufsize) {
   for (size_t i = 0; i < P.gemm.size(); ++i) {
     const OpGemm& g = P.gemm[i];
     if (!check(g.Y, g.m.n, g.c.n, "gemm.Y", i)) return msg;
-    if (g.B.buf < 0) {
+    if (g.B.buf == MV_IDENTITY) {
       if (!check(g.A, g.m.n, g.c.n, "axpy.X", i)) return msg;
+    } else if (g.B.buf == MV_ONES) {
+      if (!check(g.A, g.m.n, g.k.n, "gemm.A", i)) return msg;
     } else {
       if (!check(g.A, g.m.n, g.k.n, "gemm.A", i) || !check(g.B, g.k.n, g.c.n, "gemm.B", i)) return msg;
     }

@@ -36,7 +36,7 @@ void layout(HTree& T, int kmax);
 
 // accumulate: updates of a low-rank block are truncated together right before
 // the block is next used (accumulated updates) instead of one at a time.
-void plan_cholesky(HTree& T, Plan& P, bool accumulate = true);
+void plan_cholesky(HTree& T, Plan& P, bool accumulate = false);
 void plan_solve(HTree& T, Plan& P, int trans, int64_t voff, int64_t ncols);
 void plan_matvec(HTree& T, Plan& P, int64_t xoff, int64_t yoff, int64_t ncols);
 void plan_recompress(HTree& T, Plan& P);

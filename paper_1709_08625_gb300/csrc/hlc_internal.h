@@ -40,7 +40,10 @@ struct Dim {
 };
 
 // Y (m x c) = beta * Y + alpha * A (m x k) * B (k x c), beta in {0, 1};
-// B.buf < 0 marks B as the identity (Y = beta Y + alpha A, k = c).
+// B.buf == MV_IDENTITY marks B as the identity (Y = beta Y + alpha A, k = c),
+// B.buf == MV_ONES as the k x 1 vector of ones (a fixed-order row sum of A).
+constexpr int32_t MV_IDENTITY = -1;
+constexpr int32_t MV_ONES = -2;
 struct OpGemm {
   Mv Y, A, B;
   Dim m, k, c;
@@ -97,12 +100,13 @@ struct Bases {
   int mixed;       // 1: FP32 arithmetic for panels, products and QR (HLC_MIXED)
   int pad;
   double* flops;   // per op type algorithmic flop counters, or null
+  unsigned long long* phase;  // truncation phase cycle counters, or null
 };
 
 enum OpType : int32_t { OP_POTRF = 0, OP_TRSM = 1, OP_GEMM = 2, OP_TRUNC = 3, OP_TRUNC_BIG = 4, NOPTYPES = 5 };
 
 // Device error codes recorded in status[0].
-enum DevErr : int32_t { DEV_OK = 0, DEV_NOT_SPD = 1, DEV_RANK = 2, DEV_BAD = 3 };
+enum DevErr : int32_t { DEV_OK = 0, DEV_NOT_SPD = 1, DEV_RANK = 2, DEV_BAD = 3, DEV_TIMEOUT = 4 };
 
 // ---------------------------------------------------------------------------
 // Host-side tree.
@@ -152,6 +156,17 @@ struct Launch {
   int64_t first, count;  // range in the per-type device arrays
 };
 
+// State of the persistent kernel's grid barrier (zeroed before each launch).
+struct GridBar {
+  unsigned int count, gen, abort, pad;
+};
+
+// TRSM and GEMM op ranges of one wave (persistent execution of a plan).
+struct WaveRange {
+  int64_t trsm0, ntrsm;
+  int64_t gemm0, ngemm;
+};
+
 struct Plan {
   std::vector<OpGemm> gemm;
   std::vector<OpTrsm> trsm;
@@ -167,6 +182,9 @@ struct Plan {
   mutable cudaGraphExec_t graph = nullptr;
   mutable Bases graph_key{};
   mutable int64_t graph_kernels = 0;
+  // waves of a TRSM/GEMM-only plan, for the persistent kernel
+  std::vector<WaveRange> waves;
+  WaveRange* d_waves = nullptr;
   // device copies
   OpGemm* d_gemm = nullptr;
   OpTrsm* d_trsm = nullptr;

@@ -260,64 +260,65 @@ __global__ void k_potrf(const OpPotrf* ops, int64_t count, Bases B) {
 // TRSM: X (n x c) := L^-1 X or L^-T X, L dense lower n x n (n <= 128).
 // One warp per column of X; lane i holds rows i, i+32, i+64, i+96.
 // ---------------------------------------------------------------------------
+__device__ void do_trsm(const OpTrsm& op, const Bases& B, double* sL) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int n = op.n;
+  const int c = dimv(op.c, B.ranks);
+  if (B.flops && threadIdx.x == 0) atomicAdd(B.flops + OP_TRSM, (double)n * n * c);
+  const double* L = vptr(B, op.L);
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e % n, j = e / n;
+    sL[e] = L[i * op.L.rs + j * op.L.cs];
+  }
+  __syncthreads();
+  double* X = vptr(B, op.X);
+  for (int col = w; col < c; col += nw) {
+    double* xc = X + col * op.X.cs;
+    double x[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = lane + 32 * q;
+      x[q] = r < n ? xc[r * op.X.rs] : 0.0;
+    }
+    if (!op.trans) {
+      for (int i = 0; i < n; ++i) {
+        const int owner = i & 31, qi = i >> 5;
+        double mine = qi == 0 ? x[0] : qi == 1 ? x[1] : qi == 2 ? x[2] : x[3];
+        if (lane == owner) mine /= sL[i + i * n];
+        const double xi = __shfl_sync(0xffffffffu, mine, owner);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int r = lane + 32 * q;
+          if (r == i) x[q] = xi;
+          else if (r > i && r < n) x[q] -= sL[r + i * n] * xi;
+        }
+      }
+    } else {
+      for (int i = n - 1; i >= 0; --i) {
+        const int owner = i & 31, qi = i >> 5;
+        double mine = qi == 0 ? x[0] : qi == 1 ? x[1] : qi == 2 ? x[2] : x[3];
+        if (lane == owner) mine /= sL[i + i * n];
+        const double xi = __shfl_sync(0xffffffffu, mine, owner);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int r = lane + 32 * q;
+          if (r == i) x[q] = xi;
+          else if (r < i) x[q] -= sL[i + r * n] * xi;
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = lane + 32 * q;
+      if (r < n) xc[r * op.X.rs] = x[q];
+    }
+  }
+  __syncthreads();
+}
+
 __global__ void k_trsm(const OpTrsm* ops, int64_t count, Bases B) {
   extern __shared__ double sL[];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int64_t o = blockIdx.x; o < count; o += gridDim.x) {
-    const OpTrsm op = ops[o];
-    const int n = op.n;
-    const int c = dimv(op.c, B.ranks);
-    if (B.flops && threadIdx.x == 0) atomicAdd(B.flops + OP_TRSM, (double)n * n * c);
-    const double* L = vptr(B, op.L);
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-      const int i = e % n, j = e / n;
-      sL[e] = L[i * op.L.rs + j * op.L.cs];
-    }
-    __syncthreads();
-    double* X = vptr(B, op.X);
-    for (int col = w; col < c; col += nw) {
-      double* xc = X + col * op.X.cs;
-      double x[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int r = lane + 32 * q;
-        x[q] = r < n ? xc[r * op.X.rs] : 0.0;
-      }
-      if (!op.trans) {
-        for (int i = 0; i < n; ++i) {
-          const int owner = i & 31, qi = i >> 5;
-          double mine = qi == 0 ? x[0] : qi == 1 ? x[1] : qi == 2 ? x[2] : x[3];
-          if (lane == owner) mine /= sL[i + i * n];
-          const double xi = __shfl_sync(0xffffffffu, mine, owner);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int r = lane + 32 * q;
-            if (r == i) x[q] = xi;
-            else if (r > i && r < n) x[q] -= sL[r + i * n] * xi;
-          }
-        }
-      } else {
-        for (int i = n - 1; i >= 0; --i) {
-          const int owner = i & 31, qi = i >> 5;
-          double mine = qi == 0 ? x[0] : qi == 1 ? x[1] : qi == 2 ? x[2] : x[3];
-          if (lane == owner) mine /= sL[i + i * n];
-          const double xi = __shfl_sync(0xffffffffu, mine, owner);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int r = lane + 32 * q;
-            if (r == i) x[q] = xi;
-            else if (r < i) x[q] -= sL[i + r * n] * xi;
-          }
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int r = lane + 32 * q;
-        if (r < n) xc[r * op.X.rs] = x[q];
-      }
-    }
-    __syncthreads();
-  }
+  for (int64_t o = blockIdx.x; o < count; o += gridDim.x) do_trsm(ops[o], B, sL);
 }
 
 // ---------------------------------------------------------------------------
@@ -327,78 +328,223 @@ __global__ void k_trsm(const OpTrsm* ops, int64_t count, Bases B) {
 constexpr int GB_M = 64, GB_N = 32, GB_K = 16;
 
 template <class T>
-__global__ void __launch_bounds__(256) k_gemm(const OpGemm* ops, int64_t count, Bases B) {
-  __shared__ T As[GB_K][GB_M + 1];
-  __shared__ T Bs[GB_K][GB_N + 1];
-  const int tid = threadIdx.x, tr = tid & 15, tc = tid >> 4;
-  for (int64_t o = blockIdx.x; o < count; o += gridDim.x) {
-    const OpGemm op = ops[o];
-    const int m = dimv(op.m, B.ranks), k = dimv(op.k, B.ranks), c = dimv(op.c, B.ranks);
-    if (m <= 0 || c <= 0) continue;
-    if (B.flops && threadIdx.x == 0)
-      atomicAdd(B.flops + OP_GEMM, op.B.buf < 0 ? (double)m * c : 2.0 * m * (double)k * c);
-    double* Y = vptr(B, op.Y);
-    const double* A = vptr(B, op.A);
-    if (op.B.buf < 0) {  // Y = beta Y + alpha A
-      for (int64_t e = tid; e < (int64_t)m * c; e += blockDim.x) {
-        const int64_t i = e % m, j = e / m;
-        double* y = Y + i * op.Y.rs + j * op.Y.cs;
-        const double a = op.alpha * A[i * op.A.rs + j * op.A.cs];
-        *y = op.beta ? *y + a : a;
+struct GemmSmem {
+  T As[GB_K][GB_M + 1];
+  T Bs[GB_K][GB_N + 1];
+};
+
+// Y (m x 1) = beta Y + alpha A x: a warp per row where the rows of A are
+// contiguous (lanes stride along the row), a thread per row otherwise
+// (consecutive threads read consecutive rows); fixed summation order.
+template <class T>
+__device__ void do_gemv(const OpGemm& op, const Bases& B, int m, int k, double* Y, const double* A) {
+  const bool ones = op.B.buf == MV_ONES;
+  const double* x = ones ? nullptr : vptr(B, op.B);
+  const int64_t xs = op.B.rs;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
+  if (op.A.cs == 1 && op.A.rs != 1) {
+    for (int i = w; i < m; i += nw) {
+      const double* a = A + (int64_t)i * op.A.rs;
+      T acc = T(0);
+      if (ones)
+        for (int q = lane; q < k; q += 32) acc += (T)a[q];
+      else
+        for (int q = lane; q < k; q += 32) acc += (T)a[q] * (T)x[q * xs];
+      acc = warp_sum(acc);
+      if (lane == 0) {
+        double* yp = Y + (int64_t)i * op.Y.rs;
+        const double v = op.alpha * (double)acc;
+        *yp = op.beta ? *yp + v : v;
       }
-      continue;
     }
-    const double* Bm = vptr(B, op.B);
-    for (int ti = 0; ti < m; ti += GB_M) {
-      for (int tj = 0; tj < c; tj += GB_N) {
-        T acc[4][2];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) acc[a][0] = acc[a][1] = T(0);
-        for (int kk = 0; kk < k; kk += GB_K) {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int e = tid + q * 256;
-            const int kq = e / GB_M, iq = e % GB_M;
-            const int gi = ti + iq, gk = kk + kq;
-            As[kq][iq] = (gi < m && gk < k) ? (T)A[(int64_t)gi * op.A.rs + (int64_t)gk * op.A.cs] : T(0);
-          }
-#pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            const int e = tid + q * 256;
-            const int kq = e / GB_N, jq = e % GB_N;
-            const int gj = tj + jq, gk = kk + kq;
-            Bs[kq][jq] = (gj < c && gk < k) ? (T)Bm[(int64_t)gk * op.B.rs + (int64_t)gj * op.B.cs] : T(0);
-          }
-          __syncthreads();
-#pragma unroll
-          for (int q = 0; q < GB_K; ++q) {
-            T a[4], b[2];
-#pragma unroll
-            for (int x = 0; x < 4; ++x) a[x] = As[q][tr * 4 + x];
-            b[0] = Bs[q][tc * 2];
-            b[1] = Bs[q][tc * 2 + 1];
-#pragma unroll
-            for (int x = 0; x < 4; ++x) {
-              acc[x][0] += a[x] * b[0];
-              acc[x][1] += a[x] * b[1];
-            }
-          }
-          __syncthreads();
-        }
-#pragma unroll
-        for (int x = 0; x < 4; ++x)
-#pragma unroll
-          for (int y = 0; y < 2; ++y) {
-            const int gi = ti + tr * 4 + x, gj = tj + tc * 2 + y;
-            if (gi < m && gj < c) {
-              double* yp = Y + (int64_t)gi * op.Y.rs + (int64_t)gj * op.Y.cs;
-              const double v = op.alpha * (double)acc[x][y];
-              *yp = op.beta ? *yp + v : v;
-            }
-          }
-      }
+  } else {
+    for (int i = tid; i < m; i += blockDim.x) {
+      const double* a = A + (int64_t)i * op.A.rs;
+      T acc = T(0);
+      if (ones)
+        for (int q = 0; q < k; ++q) acc += (T)a[q * op.A.cs];
+      else
+        for (int q = 0; q < k; ++q) acc += (T)a[q * op.A.cs] * (T)x[q * xs];
+      double* yp = Y + (int64_t)i * op.Y.rs;
+      const double v = op.alpha * (double)acc;
+      *yp = op.beta ? *yp + v : v;
     }
   }
+}
+
+template <class T>
+__device__ void do_gemm(const OpGemm& op, const Bases& B, GemmSmem<T>& sm) {
+  const int tid = threadIdx.x, tr = tid & 15, tc = tid >> 4;
+  const int m = dimv(op.m, B.ranks), k = dimv(op.k, B.ranks), c = dimv(op.c, B.ranks);
+  if (m <= 0 || c <= 0) return;
+  if (B.flops && threadIdx.x == 0)
+    atomicAdd(B.flops + OP_GEMM, op.B.buf == MV_IDENTITY ? (double)m * c : 2.0 * m * (double)k * c);
+  double* Y = vptr(B, op.Y);
+  const double* A = vptr(B, op.A);
+  if (op.B.buf == MV_IDENTITY) {  // Y = beta Y + alpha A
+    for (int64_t e = tid; e < (int64_t)m * c; e += blockDim.x) {
+      const int64_t i = e % m, j = e / m;
+      double* y = Y + i * op.Y.rs + j * op.Y.cs;
+      const double a = op.alpha * A[i * op.A.rs + j * op.A.cs];
+      *y = op.beta ? *y + a : a;
+    }
+    return;
+  }
+  if (c == 1 || op.B.buf == MV_ONES) {
+    if (k > 0) do_gemv<T>(op, B, m, k, Y, A);
+    return;
+  }
+  const double* Bm = vptr(B, op.B);
+  for (int ti = 0; ti < m; ti += GB_M) {
+    for (int tj = 0; tj < c; tj += GB_N) {
+      T acc[4][2];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) acc[a][0] = acc[a][1] = T(0);
+      for (int kk = 0; kk < k; kk += GB_K) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int e = tid + q * 256;
+          const int kq = e / GB_M, iq = e % GB_M;
+          const int gi = ti + iq, gk = kk + kq;
+          sm.As[kq][iq] = (gi < m && gk < k) ? (T)A[(int64_t)gi * op.A.rs + (int64_t)gk * op.A.cs] : T(0);
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int e = tid + q * 256;
+          const int kq = e / GB_N, jq = e % GB_N;
+          const int gj = tj + jq, gk = kk + kq;
+          sm.Bs[kq][jq] = (gj < c && gk < k) ? (T)Bm[(int64_t)gk * op.B.rs + (int64_t)gj * op.B.cs] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < GB_K; ++q) {
+          T a[4], b[2];
+#pragma unroll
+          for (int x = 0; x < 4; ++x) a[x] = sm.As[q][tr * 4 + x];
+          b[0] = sm.Bs[q][tc * 2];
+          b[1] = sm.Bs[q][tc * 2 + 1];
+#pragma unroll
+          for (int x = 0; x < 4; ++x) {
+            acc[x][0] += a[x] * b[0];
+            acc[x][1] += a[x] * b[1];
+          }
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 2; ++y) {
+          const int gi = ti + tr * 4 + x, gj = tj + tc * 2 + y;
+          if (gi < m && gj < c) {
+            double* yp = Y + (int64_t)gi * op.Y.rs + (int64_t)gj * op.Y.cs;
+            const double v = op.alpha * (double)acc[x][y];
+            *yp = op.beta ? *yp + v : v;
+          }
+        }
+    }
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_gemm(const OpGemm* ops, int64_t count, Bases B) {
+  __shared__ GemmSmem<T> sm;
+  for (int64_t o = blockIdx.x; o < count; o += gridDim.x) do_gemm<T>(ops[o], B, sm);
+}
+
+// Grid-wide barrier of the persistent kernel.  Thread 0 of each CTA arrives
+// on a counter; the last CTA to arrive resets it and advances the generation
+// the others wait on.  The wait is bounded: after kBarrierNs, or once another
+// CTA has given up, the CTA records DEV_TIMEOUT, raises the abort flag and
+// every CTA leaves the kernel at its next barrier.
+constexpr unsigned long long kBarrierNs = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ bool grid_barrier(GridBar* gb, int* status) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* gen = &gb->gen;
+    volatile unsigned int* abort = &gb->abort;
+    int good = *abort == 0;
+    if (good) {
+      const unsigned int g = *gen;
+      __threadfence();
+      if (atomicAdd(&gb->count, 1u) == gridDim.x - 1) {
+        atomicExch(&gb->count, 0u);
+        __threadfence();
+        atomicAdd(&gb->gen, 1u);
+      } else {
+        const unsigned long long t0 = global_ns();
+        while (*gen == g) {
+          if (*abort || global_ns() - t0 > kBarrierNs) {
+            atomicExch(&gb->abort, 1u);
+            record_error(status, DEV_TIMEOUT, 0);
+            good = 0;
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+      __threadfence();
+    }
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// Persistent execution of a plan made of TRSM and GEMM ops (the solves and
+// the matvec): one cooperative launch (all CTAs co-resident) walks the waves;
+// within a wave the CTAs take the ops round-robin, and a grid barrier
+// separates consecutive waves.
+__global__ void __launch_bounds__(256) k_waves(const WaveRange* waves, int nwaves, const OpTrsm* trsm,
+                                               const OpGemm* gemm, Bases B, GridBar* gb) {
+  extern __shared__ double sL[];
+  __shared__ GemmSmem<double> gd;
+  __shared__ GemmSmem<float> gf;
+  for (int w = 0; w < nwaves; ++w) {
+    const WaveRange wr = waves[w];
+    const int64_t tot = wr.ntrsm + wr.ngemm;
+    for (int64_t o = blockIdx.x; o < tot; o += gridDim.x) {
+      if (o < wr.ntrsm) {
+        do_trsm(trsm[wr.trsm0 + o], B, sL);
+      } else if (B.mixed) {
+        do_gemm<float>(gemm[wr.gemm0 + (o - wr.ntrsm)], B, gf);
+      } else {
+        do_gemm<double>(gemm[wr.gemm0 + (o - wr.ntrsm)], B, gd);
+      }
+    }
+    if (w + 1 < nwaves && !grid_barrier(gb, B.status)) return;
+  }
+}
+
+int waves_grid(int max_dense) {
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_waves, 256,
+                                                    (size_t)max_dense * max_dense * sizeof(double)) != cudaSuccess)
+    return 0;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return per * sms;
+}
+
+int launch_waves(const WaveRange* waves, int nwaves, const OpTrsm* trsm, const OpGemm* gemm, const Bases& B,
+                 GridBar* gb, int max_dense, cudaStream_t st) {
+  const int grid = waves_grid(max_dense);
+  if (grid <= 0 || nwaves <= 0 || !gb) return -1;
+  if (cudaMemsetAsync(gb, 0, sizeof(GridBar), st) != cudaSuccess) return -1;
+  void* args[] = {(void*)&waves, (void*)&nwaves, (void*)&trsm, (void*)&gemm, (void*)&B, (void*)&gb};
+  return cudaLaunchCooperativeKernel((void*)k_waves, grid, 256, args, (size_t)max_dense * max_dense * sizeof(double),
+                                     st) == cudaSuccess
+             ? 0
+             : -1;
 }
 
 // ---------------------------------------------------------------------------
@@ -537,8 +683,9 @@ int configure_kernels(int max_dense) {
   const size_t need = (size_t)max_dense * max_dense * sizeof(double);
   cudaError_t e1 = cudaFuncSetAttribute(k_potrf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
   cudaError_t e2 = cudaFuncSetAttribute(k_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+  cudaError_t e4 = cudaFuncSetAttribute(k_waves, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
   const int e3 = configure_trunc();
-  return (e1 == cudaSuccess && e2 == cudaSuccess && e3 == 0) ? 0 : -1;
+  return (e1 == cudaSuccess && e2 == cudaSuccess && e3 == 0 && e4 == cudaSuccess) ? 0 : -1;
 }
 
 }  // namespace hlc

@@ -124,6 +124,9 @@ int hlc_serve_start(hlc_ctx* ctx, size_t budget, int max_slots) {
       for (hlc_ctx* x : s->slot_ctx) hlc_destroy(x);
       return st;
     }
+    // Slots share the SMs, so their solves use wave-by-wave launches: a
+    // grid-barrier kernel needs all of its CTAs resident at once.
+    set_persistent(c, false);
     s->slot_ctx.push_back(c);
   }
   for (int i = 0; i < max_slots; ++i) s->workers.emplace_back(worker, s.get(), i);

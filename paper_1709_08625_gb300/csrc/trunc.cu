@@ -9,17 +9,20 @@
 //
 //   1. R_u, R_v: R factors of Ucat and Vcat by Householder QR streamed over
 //      row chunks ([R; chunk] -> R); Q is never formed;
-//   2. M = R_u R_v^T (K x K, FP64);
-//   3. the SVD of M in FP64: QR with column pivoting reduces M to its
+//   2. M = R_u R_v^T (K x K);
+//   3. the SVD of M: QR with column pivoting reduces M to its
 //      numerical rank r (the trailing part dropped is below 1e-3 eps |M|),
 //      then one-sided Jacobi on the r columns of (R P^T)^T: M = X S Y^T;
 //   4. keep the k values sigma_i > eps sigma_1 and write
 //        U_new = Ucat R_v^T Y_k S_k^-1/2 = Q_u X_k S_k^1/2,
-//        V_new = Vcat R_u^T X_k S_k^-1/2 = Q_v Y_k S_k^1/2,
-//      row by row, in place.
+//        V_new = Vcat R_u^T X_k G^-1 S_k^-1/2,  G = X_k^T X_k (~ I),
+//      row by row, in place (G^-1 makes U_new V_new^T the orthogonal
+//      projection of the block onto span(Q_u X_k) even where the computed
+//      X_k is not exactly orthonormal).
 //
-// Steps 1 and 4 run in FP64 (HLC_FP64) or FP32 (HLC_MIXED); step 3 is FP64
-// in both.  Targets with m + n above TR_BIG_ROWS run on a cluster of TR_CL
+// Every step runs in FP64 (HLC_FP64) or FP32 (HLC_MIXED).  In FP32 the R
+// factors carry FP32 rounding already, so the core's SVD is taken in the
+// same type; its stopping rules scale with the type's unit roundoff.  Targets with m + n above TR_BIG_ROWS run on a cluster of TR_CL
 // CTAs: each CTA streams its share of the rows, CTAs 0 and 1 combine the
 // partial R factors, CTA 0 computes the core, all CTAs apply; the phases are
 // separated by cluster barriers.
@@ -40,33 +43,34 @@ namespace hlc {
 constexpr int TR_KB = 64;      // new columns per batch
 constexpr int TR_KT = 256;     // columns of one truncation: rank (<= 128) + batch (<= 128)
 constexpr int TR_KCAP = 128;   // rank capacity of a block
-// rows per streamed chunk: 64 KB of shared memory either way (3 CTAs per SM)
+// the streamed chunk buffer: 64 KB of shared memory either way (3 CTAs per
+// SM); a chunk has as many rows as fit for the batch's K (at least 32)
 template <class T>
 struct TrCh {
-  static constexpr int value = sizeof(T) == 8 ? 32 : 64;
+  static constexpr int value = sizeof(T) == 8 ? 32 : 64;  // rows at K = TR_KT
+  static constexpr int elems = value * TR_KT;
 };
 constexpr int TR_THREADS = 256;
-constexpr int TR_OUT_LD = TR_KCAP + 1;
 constexpr int TR_CL = 8;       // CTAs per cluster for large targets
 constexpr int64_t TR_REG = (int64_t)TR_KT * TR_KT;
-// per-CTA scratch: Pu, Pv, M, W, J, X (K x K each), Cu, Cv (K x 128 each),
-// the apply stage, and a few words for cluster broadcasts
+// per-CTA scratch: Pu, Pv, M, W, J, X (K x K each), Cu, Cv (K x 128 each)
+// and a few words for cluster broadcasts
 constexpr int64_t TR_PANEL = (int64_t)TR_KT * TR_KCAP;
 constexpr int64_t TR_OFF_X = 5 * TR_REG;
 constexpr int64_t TR_OFF_CU = TR_OFF_X + TR_REG;  // X holds the rank x rank Jacobi matrix
 constexpr int64_t TR_OFF_CV = TR_OFF_CU + TR_PANEL;
-constexpr int64_t TR_OFF_STAGE = TR_OFF_CV + TR_PANEL;
-constexpr int64_t TR_OFF_FLAG = TR_OFF_STAGE + (int64_t)TR_THREADS * TR_OUT_LD;
+constexpr int64_t TR_OFF_FLAG = TR_OFF_CV + TR_PANEL;
 constexpr int64_t TR_SCRATCH = TR_OFF_FLAG + 8;
 
 int64_t trunc_scratch_doubles() { return TR_SCRATCH; }
 int max_trunc_ctas() { return 152 * 3; }
 
 struct TrCat {
-  int kacc;            // leading columns from the target itself
-  int nt;              // terms in the batch
-  const TermD* terms;  // batch terms
-  int col0[65];        // first concatenated column of each term; col0[nt] = K
+  int kacc;                   // leading columns from the target itself
+  int nt;                     // terms in the batch
+  const TermD* terms;         // batch terms
+  int col0[65];               // first concatenated column of each term; col0[nt] = K
+  unsigned char tcol[TR_KT];  // term of every concatenated column beyond kacc
 };
 
 __device__ __forceinline__ int term_cols(const TermD& d, const int* ranks) {
@@ -80,8 +84,7 @@ __device__ __forceinline__ double cat_value(const Bases& B, const OpTrunc& op, c
     return side == 0 ? B.buf[op.U.buf][op.U.off + row + (int64_t)col * op.m]
                      : B.buf[op.V.buf][op.V.off + row + (int64_t)col * op.n];
   }
-  int t = 0;
-  while (col >= cat.col0[t + 1]) ++t;
+  const int t = cat.tcol[col];
   const TermD& d = cat.terms[t];
   const int lc = col - cat.col0[t];
   if (side == 0) {
@@ -101,7 +104,7 @@ __device__ __forceinline__ double cat_value(const Bases& B, const OpTrunc& op, c
 // matrix whose entries rowval(i, c) returns.  sC: TrCh<T> x K chunk buffer.
 template <class T, class F>
 __device__ void qr_stream(F rowval, int nrows, int K, T* R, T* sC, double* sh) {
-  constexpr int TR_CH = TrCh<T>::value;
+  const int TR_CH = max(32, (TrCh<T>::elems / max(K, 1)) & ~31);
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
   for (int e = tid; e < K * K; e += blockDim.x) R[(e % K) + (int64_t)(e / K) * TR_KT] = T(0);
   __syncthreads();
@@ -148,60 +151,87 @@ __device__ void qr_stream(F rowval, int nrows, int K, T* R, T* sC, double* sh) {
   }
 }
 
+template <class T>
 struct CoreShared {
-  double cn[TR_KT];
-  double tauq[TR_KT];
-  double sv[TR_KT];
+  T cn[TR_KT];
+  T tauq[TR_KT];
+  T sv[TR_KT];
   int piv[TR_KT];
   int order[TR_KT];
-  double red[40];
+  T red[40];
   int stop, jmax, rank, k, rot;
 };
 
 // FP64 core: SVD of M = R_u R_v^T reduced by column-pivoted QR, truncation
 // rank, and the coefficient matrices Cu, Cv (K x k, ld TR_KT).
+__device__ __forceinline__ void phase_mark(unsigned long long* ph, int slot, long long& t) {
+  if (ph && threadIdx.x == 0) {
+    const long long now = clock64();
+    atomicAdd(ph + slot, (unsigned long long)(now - t));
+    t = now;
+  }
+}
+
 template <class T>
-__device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, double* M, double* W, double* J,
-                        double* X, double* Cu, double* Cv, CoreShared& cs, int* status) {
+__device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, T* M, T* W, T* J, T* X, T* Cu, T* Cv,
+                        CoreShared<T>& cs, int* status,
+                        unsigned long long* ph = nullptr) {
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
+  long long t0 = clock64();
   // M = Ru Rv^T (both upper triangular)
   for (int e = tid; e < K * K; e += blockDim.x) {
     const int i = e % K, j = e / K;
-    double s = 0.0;
-    for (int c = max(i, j); c < K; ++c) s += (double)Ru[i + (int64_t)c * TR_KT] * (double)Rv[j + (int64_t)c * TR_KT];
+    T s = T(0);
+    for (int c = max(i, j); c < K; ++c) s += Ru[i + (int64_t)c * TR_KT] * Rv[j + (int64_t)c * TR_KT];
     M[i + (int64_t)j * TR_KT] = s;
   }
   for (int j = tid; j < K; j += blockDim.x) cs.piv[j] = j;
   __syncthreads();
-  // Householder QR with column pivoting, stopped at the numerical rank
-  double ref = 0.0;
-  int r = 0;
+  phase_mark(ph, 3, t0);
+  // Householder QR with column pivoting, stopped at the numerical rank: the
+  // remaining columns are dropped once their norm is below 1e-3 eps |M|
+  // (or 8 unit roundoffs of the core type, when that is larger)
+  const T stop_rel = (T)fmax(1e-3 * eps, sizeof(T) == 8 ? 8.0 * 2.220446049250313e-16 : 8.0 * 1.1920929e-7);
+    int r = 0;
   for (; r < K; ++r) {
     for (int j = r + w; j < K; j += nw) {
-      double p = 0.0;
+      T p = T(0);
       for (int i = r + lane; i < K; i += 32) p += M[i + (int64_t)j * TR_KT] * M[i + (int64_t)j * TR_KT];
       p = warp_sum(p);
       if (lane == 0) cs.cn[j] = p;
     }
     __syncthreads();
-    if (tid == 0) {
-      int jm = r;
-      double rem = 0.0;
-      for (int j = r; j < K; ++j) {
+    if (w == 0) {
+      int jm = -1;
+      T best = T(-1), rem = T(0);
+      for (int j = r + lane; j < K; j += 32) {
         rem += cs.cn[j];
-        if (cs.cn[j] > cs.cn[jm]) jm = j;
+        if (cs.cn[j] > best) {
+          best = cs.cn[j];
+          jm = j;
+        }
       }
-      cs.jmax = jm;
-      if (r == 0) cs.red[0] = sqrt(cs.cn[jm]);
-      cs.stop = (cs.red[0] == 0.0) || !(sqrt(rem) > 1e-3 * eps * cs.red[0]);
+      rem = warp_sum(rem);
+      for (int o = 16; o > 0; o >>= 1) {  // max, ties to the smaller index
+        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, jm, o);
+        if (ob > best || (ob == best && oj >= 0 && (jm < 0 || oj < jm))) {
+          best = ob;
+          jm = oj;
+        }
+      }
+      if (lane == 0) {
+        cs.jmax = jm;
+        if (r == 0) cs.red[0] = sqrt(best);
+        cs.stop = (cs.red[0] == T(0)) || !(sqrt(rem) > stop_rel * cs.red[0]);
+      }
     }
     __syncthreads();
-    ref = cs.red[0];
     if (cs.stop) break;
     const int jm = cs.jmax;
     if (jm != r) {
       for (int i = tid; i < K; i += blockDim.x) {
-        const double a = M[i + (int64_t)r * TR_KT];
+        const T a = M[i + (int64_t)r * TR_KT];
         M[i + (int64_t)r * TR_KT] = M[i + (int64_t)jm * TR_KT];
         M[i + (int64_t)jm * TR_KT] = a;
       }
@@ -213,17 +243,17 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, d
     }
     __syncthreads();
     if (w == 0) {
-      double xn = 0.0;
+      T xn = T(0);
       for (int i = r + 1 + lane; i < K; i += 32) xn += M[i + (int64_t)r * TR_KT] * M[i + (int64_t)r * TR_KT];
       xn = warp_sum(xn);
-      const double alpha = M[r + (int64_t)r * TR_KT];
-      double tau = 0.0, sc = 0.0, beta = alpha;
-      if (xn > 0.0) {
+      const T alpha = M[r + (int64_t)r * TR_KT];
+      T tau = T(0), sc = T(0), beta = alpha;
+      if (xn > T(0)) {
         beta = -copysign(sqrt(alpha * alpha + xn), alpha);
         tau = (beta - alpha) / beta;
-        sc = 1.0 / (alpha - beta);
+        sc = T(1) / (alpha - beta);
       }
-      if (tau != 0.0)
+      if (tau != T(0))
         for (int i = r + 1 + lane; i < K; i += 32) M[i + (int64_t)r * TR_KT] *= sc;
       if (lane == 0) {
         M[r + (int64_t)r * TR_KT] = beta;
@@ -231,13 +261,13 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, d
       }
     }
     __syncthreads();
-    const double tau = cs.tauq[r];
-    if (tau != 0.0) {
+    const T tau = cs.tauq[r];
+    if (tau != T(0)) {
       for (int l = r + 1 + w; l < K; l += nw) {
-        double p = 0.0;
+        T p = T(0);
         for (int i = r + 1 + lane; i < K; i += 32) p += M[i + (int64_t)r * TR_KT] * M[i + (int64_t)l * TR_KT];
         p = warp_sum(p);
-        const double wv = tau * (p + M[r + (int64_t)l * TR_KT]);
+        const T wv = tau * (p + M[r + (int64_t)l * TR_KT]);
         for (int i = r + 1 + lane; i < K; i += 32) M[i + (int64_t)l * TR_KT] -= wv * M[i + (int64_t)r * TR_KT];
         if (lane == 0) M[r + (int64_t)l * TR_KT] -= wv;
       }
@@ -245,8 +275,9 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, d
     __syncthreads();
   }
   const int rank = r;
-  (void)ref;
   (void)X;
+  phase_mark(ph, 4, t0);
+  if (ph && tid == 0) atomicAdd(ph + 10, (unsigned long long)rank);
   if (rank == 0) {
     if (tid == 0) cs.k = 0;
     __syncthreads();
@@ -255,7 +286,7 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, d
   // B = (R P^T)^T (K x rank) into W
   for (int e = tid; e < K * rank; e += blockDim.x) {
     const int j = e % K, i = e / K;  // R(i, j) -> B(piv[j], i)
-    W[cs.piv[j] + (int64_t)i * TR_KT] = (i <= j) ? M[i + (int64_t)j * TR_KT] : 0.0;
+    W[cs.piv[j] + (int64_t)i * TR_KT] = (i <= j) ? M[i + (int64_t)j * TR_KT] : T(0);
   }
   __syncthreads();
   // Householder QR of B (K x rank): B = Q_B R_B; the one-sided Jacobi then
@@ -263,17 +294,17 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, d
   // SVD), and the left vectors of B are Q_B times those of R_B.
   for (int q = 0; q < rank; ++q) {
     if (w == 0) {
-      double xn = 0.0;
+      T xn = T(0);
       for (int i = q + 1 + lane; i < K; i += 32) xn += W[i + (int64_t)q * TR_KT] * W[i + (int64_t)q * TR_KT];
       xn = warp_sum(xn);
-      const double alpha = W[q + (int64_t)q * TR_KT];
-      double tau = 0.0, sc = 0.0, beta = alpha;
-      if (xn > 0.0) {
+      const T alpha = W[q + (int64_t)q * TR_KT];
+      T tau = T(0), sc = T(0), beta = alpha;
+      if (xn > T(0)) {
         beta = -copysign(sqrt(alpha * alpha + xn), alpha);
         tau = (beta - alpha) / beta;
-        sc = 1.0 / (alpha - beta);
+        sc = T(1) / (alpha - beta);
       }
-      if (tau != 0.0)
+      if (tau != T(0))
         for (int i = q + 1 + lane; i < K; i += 32) W[i + (int64_t)q * TR_KT] *= sc;
       if (lane == 0) {
         W[q + (int64_t)q * TR_KT] = beta;
@@ -281,36 +312,44 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, d
       }
     }
     __syncthreads();
-    const double tau = cs.cn[q];
-    if (tau != 0.0) {
+    const T tau = cs.cn[q];
+    if (tau != T(0)) {
       for (int l = q + 1 + w; l < rank; l += nw) {
-        double p = 0.0;
+        T p = T(0);
         for (int i = q + 1 + lane; i < K; i += 32) p += W[i + (int64_t)q * TR_KT] * W[i + (int64_t)l * TR_KT];
         p = warp_sum(p);
-        const double wv = tau * (p + W[q + (int64_t)l * TR_KT]);
+        const T wv = tau * (p + W[q + (int64_t)l * TR_KT]);
         for (int i = q + 1 + lane; i < K; i += 32) W[i + (int64_t)l * TR_KT] -= wv * W[i + (int64_t)q * TR_KT];
         if (lane == 0) W[q + (int64_t)l * TR_KT] -= wv;
       }
     }
     __syncthreads();
   }
-  // R_B (upper triangle of W's first rank rows) becomes the Jacobi matrix A
-  // (X region); J accumulates its rotations.
-  double* A = X;
+  // The one-sided Jacobi works on A = R_B^T (lower triangular; the
+  // transpose of the triangular factor is what the QR preconditioning makes
+  // nearly orthogonal), in the X region; J accumulates its rotations.
+  T* A = X;
   for (int e = tid; e < rank * rank; e += blockDim.x) {
     const int i = e % rank, j = e / rank;
-    A[i + (int64_t)j * TR_KT] = (i <= j) ? W[i + (int64_t)j * TR_KT] : 0.0;
-    J[i + (int64_t)j * TR_KT] = (i == j) ? 1.0 : 0.0;
+    A[i + (int64_t)j * TR_KT] = (i >= j) ? W[j + (int64_t)i * TR_KT] : T(0);
+    J[i + (int64_t)j * TR_KT] = (i == j) ? T(1) : T(0);
   }
   __syncthreads();
   // one-sided Jacobi on the rank columns of A, round-robin pairs
-  double fro2 = 0.0;
+  T fro2 = T(0);
   for (int e = tid; e < rank * rank; e += blockDim.x) {
-    const double v = A[(e % rank) + (int64_t)(e / rank) * TR_KT];
+    const T v = A[(e % rank) + (int64_t)(e / rank) * TR_KT];
     fro2 += v * v;
   }
   fro2 = block_sum(fro2, cs.red + 1);
-  const double tiny = 1e-34 * fro2;
+  // pairs of columns both at rounding level (below 1e-13 |A|_F in FP64,
+  // 1e-6 |A|_F in FP32) cannot affect any truncation decision and are left
+  // alone; a pair is rotated while |gamma| > max(rank, 16) c sqrt(alpha beta)
+  // with c = 1e-14 (FP64) or 1e-6 (FP32), i.e. some tens of unit roundoffs
+  // per column: the columns end up orthogonal far below any truncation
+  // threshold, without chasing the rounding noise of the dot products
+  const T tiny = (sizeof(T) == 8 ? T(1e-26) : T(1e-12)) * fro2;
+  const T rtol = (T)max(rank, 16) * (sizeof(T) == 8 ? T(1e-14) : T(1e-6));
   const int Kp = rank + (rank & 1);
   for (int sweep = 0; sweep < 80 && Kp > 1; ++sweep) {
     if (tid == 0) cs.rot = 0;
@@ -326,9 +365,9 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, d
           b = t;
         }
         if (b >= rank) continue;
-        double al = 0.0, be = 0.0, ga = 0.0;
+        T al = T(0), be = T(0), ga = T(0);
         for (int i = lane; i < rank; i += 32) {
-          const double x = A[i + (int64_t)a * TR_KT], y = A[i + (int64_t)b * TR_KT];
+          const T x = A[i + (int64_t)a * TR_KT], y = A[i + (int64_t)b * TR_KT];
           al += x * x;
           be += y * y;
           ga += x * y;
@@ -337,15 +376,15 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, d
         be = warp_sum(be);
         ga = warp_sum(ga);
         if (al <= tiny && be <= tiny) continue;
-        if (ga == 0.0 || fabs(ga) <= 1e-15 * sqrt(al * be)) continue;
-        const double zeta = (be - al) / (2.0 * ga);
-        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+        if (ga == T(0) || fabs(ga) <= rtol * sqrt(al * be)) continue;
+        const T zeta = (be - al) / (T(2) * ga);
+        const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+        const T c = T(1) / sqrt(T(1) + t * t), sn = c * t;
         for (int i = lane; i < rank; i += 32) {
-          const double x = A[i + (int64_t)a * TR_KT], y = A[i + (int64_t)b * TR_KT];
+          const T x = A[i + (int64_t)a * TR_KT], y = A[i + (int64_t)b * TR_KT];
           A[i + (int64_t)a * TR_KT] = c * x - sn * y;
           A[i + (int64_t)b * TR_KT] = sn * x + c * y;
-          const double jx = J[i + (int64_t)a * TR_KT], jy = J[i + (int64_t)b * TR_KT];
+          const T jx = J[i + (int64_t)a * TR_KT], jy = J[i + (int64_t)b * TR_KT];
           J[i + (int64_t)a * TR_KT] = c * jx - sn * jy;
           J[i + (int64_t)b * TR_KT] = sn * jx + c * jy;
         }
@@ -356,9 +395,10 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, d
     if (!cs.rot) break;
     __syncthreads();
   }
+  phase_mark(ph, 5, t0);
   // singular values, order (ties: smaller index first), truncation rank
   for (int j = w; j < rank; j += nw) {
-    double s = 0.0;
+    T s = T(0);
     for (int i = lane; i < rank; i += 32) s += A[i + (int64_t)j * TR_KT] * A[i + (int64_t)j * TR_KT];
     s = warp_sum(s);
     if (lane == 0) cs.sv[j] = sqrt(s);
@@ -371,10 +411,11 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, d
   }
   __syncthreads();
   if (tid == 0) {
-    const double smax = cs.sv[cs.order[0]];
+    const T smax = cs.sv[cs.order[0]];
+    const T thr = (T)eps * smax;
     int k = 0;
-    if (smax > 0.0)
-      while (k < rank && cs.sv[cs.order[k]] > eps * smax) ++k;
+    if (smax > T(0))
+      while (k < rank && cs.sv[cs.order[k]] > thr) ++k;
     if (!(smax == smax)) {
       record_error(status, DEV_BAD, 1);
       k = 0;
@@ -387,79 +428,147 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, d
   }
   __syncthreads();
   const int k = cs.k;
-  // With B = P R^T = Q_B A J^T... the Jacobi gives A J = Wa (orthogonal
-  // columns), so B = Q_B Wa J^T and M = Q R P^T = Q B^T = (Q J) S (Q_B Wa_n)^T:
-  //   left vectors of M:  x_c = Q [J(:, j_c); 0]      (reflectors of the pivoted QR, in M)
-  //   right vectors of M: y_c = Q_B [Wa_n(:, j_c); 0]  (reflectors of the QR of B, in W)
+  // The Jacobi gives R_B^T J = Wa (orthogonal columns, Wa = Wa_n S), so
+  // R_B = J S Wa_n^T, B = Q_B R_B = (Q_B J) S Wa_n^T, and with M = Q R P^T =
+  // Q B^T = (Q Wa_n) S (Q_B J)^T:
+  //   left vectors of M:  x_c = Q [Wa_n(:, j_c); 0]  (reflectors of the pivoted QR, in M)
+  //   right vectors of M: y_c = Q_B [J(:, j_c); 0]   (reflectors of the QR of B, in W)
   // Both are built in the Cu/Cv regions' columns (K x k each) before the
   // coefficients overwrite them: x_c in Cv, y_c in Cu.
   for (int c = w; c < k; c += nw) {
     const int j = cs.order[c];
-    const double sv = cs.sv[j];
-    double* x = Cv + (int64_t)c * TR_KT;
-    double* y = Cu + (int64_t)c * TR_KT;
+    const T sv = cs.sv[j];
+    T* x = Cv + (int64_t)c * TR_KT;
+    T* y = Cu + (int64_t)c * TR_KT;
     for (int i = lane; i < K; i += 32) {
-      x[i] = i < rank ? J[i + (int64_t)j * TR_KT] : 0.0;
-      y[i] = i < rank ? A[i + (int64_t)j * TR_KT] / sv : 0.0;
+      x[i] = i < rank ? A[i + (int64_t)j * TR_KT] / sv : T(0);
+      y[i] = i < rank ? J[i + (int64_t)j * TR_KT] : T(0);
     }
     __syncwarp();
     for (int q = rank - 1; q >= 0; --q) {
-      const double tq = cs.tauq[q], tb = cs.cn[q];
-      double p = 0.0, pb = 0.0;
+      const T tq = cs.tauq[q], tb = cs.cn[q];
+      T p = T(0), pb = T(0);
       for (int i = q + lane; i < K; i += 32) {
-        p += (i == q ? 1.0 : M[i + (int64_t)q * TR_KT]) * x[i];
-        pb += (i == q ? 1.0 : W[i + (int64_t)q * TR_KT]) * y[i];
+        p += (i == q ? T(1) : M[i + (int64_t)q * TR_KT]) * x[i];
+        pb += (i == q ? T(1) : W[i + (int64_t)q * TR_KT]) * y[i];
       }
       p = warp_sum(p);
       pb = warp_sum(pb);
       for (int i = q + lane; i < K; i += 32) {
-        if (tq != 0.0) x[i] -= tq * p * (i == q ? 1.0 : M[i + (int64_t)q * TR_KT]);
-        if (tb != 0.0) y[i] -= tb * pb * (i == q ? 1.0 : W[i + (int64_t)q * TR_KT]);
+        if (tq != T(0)) x[i] -= tq * p * (i == q ? T(1) : M[i + (int64_t)q * TR_KT]);
+        if (tb != T(0)) y[i] -= tb * pb * (i == q ? T(1) : W[i + (int64_t)q * TR_KT]);
       }
       __syncwarp();
     }
   }
   __syncthreads();
-  // Cu = R_v^T y_c / s^0.5 ; Cv = R_u^T x_c / s^0.5 (in place: column c of
-  // Cu / Cv holds y_c / x_c; each thread finishes a whole column)
-  for (int c = tid; c < k; c += blockDim.x) {
-    const double isq = 1.0 / sqrt(cs.sv[cs.order[c]]);
-    double* y = Cu + (int64_t)c * TR_KT;
-    double* x = Cv + (int64_t)c * TR_KT;
-    for (int col = K - 1; col >= 0; --col) {  // R^T is lower: row col needs entries p <= col
-      double a = 0.0, b = 0.0;
-      for (int p = 0; p <= col; ++p) {
-        a += (double)Rv[p + (int64_t)col * TR_KT] * y[p];
-        b += (double)Ru[p + (int64_t)col * TR_KT] * x[p];
+  // G = X_k^T X_k, the Gram matrix of the kept left vectors (the identity up
+  // to the orthogonality the Jacobi reached), lower triangle in the X region
+  // (A is no longer needed).  V_new carries G^-1: then U_new V_new^T =
+  // Q_u P M Q_v^T with P the orthogonal projector onto span(X_k), whose
+  // distance from M is bounded by the dropped columns whether or not X_k is
+  // exactly orthogonal (in FP32 it is only to ~1e-6, which is not below eps).
+  T* G = X;
+  for (int e = tid; e < k * k; e += blockDim.x) {
+    const int i = e % k, j = e / k;
+    if (i < j) continue;
+    const T* xi = Cv + (int64_t)i * TR_KT;
+    const T* xj = Cv + (int64_t)j * TR_KT;
+    T g = T(0);
+    for (int q = 0; q < K; ++q) g += xi[q] * xj[q];
+    G[i + (int64_t)j * TR_KT] = g;
+  }
+  __syncthreads();
+  // G = L L^T in place (warp 0, left-looking); G is near the identity, so a
+  // pivot below 1/4 means the vectors are unusable and the correction is
+  // skipped
+  if (w == 0) {
+    int ok = 1;
+    for (int j = 0; j < k; ++j) {
+      T part = T(0);
+      for (int q = lane; q < j; q += 32) part += G[j + (int64_t)q * TR_KT] * G[j + (int64_t)q * TR_KT];
+      part = warp_sum(part);
+      const T d = G[j + (int64_t)j * TR_KT] - part;
+      if (!(d > T(0.25))) ok = 0;
+      const T ljj = sqrt(d > T(0.25) ? d : T(1));
+      for (int i = j + 1 + lane; i < k; i += 32) {
+        T g = G[i + (int64_t)j * TR_KT];
+        for (int q = 0; q < j; ++q) g -= G[i + (int64_t)q * TR_KT] * G[j + (int64_t)q * TR_KT];
+        G[i + (int64_t)j * TR_KT] = g / ljj;
       }
-      y[col] = a * isq;
-      x[col] = b * isq;
+      __syncwarp();
+      if (lane == 0) G[j + (int64_t)j * TR_KT] = ljj;
+      __syncwarp();
+    }
+    if (lane == 0) cs.rot = ok;
+  }
+  // Cu = R_v^T y_c / s^0.5 and Cv = R_u^T x_c, one entry per thread; y_c,
+  // x_c sit in Cu, Cv, the results go to W, M (free now)
+  for (int e = tid; e < K * k; e += blockDim.x) {
+    const int col = e % K, c = e / K;
+    const T isq = T(1) / sqrt(cs.sv[cs.order[c]]);
+    const T* y = Cu + (int64_t)c * TR_KT;
+    const T* x = Cv + (int64_t)c * TR_KT;
+    T a = T(0), b = T(0);
+    for (int q = 0; q <= col; ++q) {
+      a += Rv[q + (int64_t)col * TR_KT] * y[q];
+      b += Ru[q + (int64_t)col * TR_KT] * x[q];
+    }
+    W[col + (int64_t)c * TR_KT] = a * isq;
+    M[col + (int64_t)c * TR_KT] = b;
+  }
+  __syncthreads();
+  // each row of R_u^T X_k times G^-1 (one thread per row), then S^-1/2
+  if (cs.rot) {
+    for (int col = tid; col < K; col += blockDim.x) {
+      T* row = M + col;
+      for (int c = 0; c < k; ++c) {
+        T v = row[(int64_t)c * TR_KT];
+        for (int q = 0; q < c; ++q) v -= G[c + (int64_t)q * TR_KT] * row[(int64_t)q * TR_KT];
+        row[(int64_t)c * TR_KT] = v / G[c + (int64_t)c * TR_KT];
+      }
+      for (int c = k - 1; c >= 0; --c) {
+        T v = row[(int64_t)c * TR_KT];
+        for (int q = c + 1; q < k; ++q) v -= G[q + (int64_t)c * TR_KT] * row[(int64_t)q * TR_KT];
+        row[(int64_t)c * TR_KT] = v / G[c + (int64_t)c * TR_KT];
+      }
     }
   }
   __syncthreads();
+  for (int e = tid; e < K * k; e += blockDim.x) {
+    const int col = e % K, c = e / K;
+    const T isq = T(1) / sqrt(cs.sv[cs.order[c]]);
+    Cu[col + (int64_t)c * TR_KT] = W[col + (int64_t)c * TR_KT];
+    Cv[col + (int64_t)c * TR_KT] = M[col + (int64_t)c * TR_KT] * isq;
+  }
+  __syncthreads();
+  phase_mark(ph, 6, t0);
 }
 
-// Rows [r0, r1) of one side: out(row, c) = sum_col cat(row, col) C(col, c).
+// Rows [r0, r1) of one side: out(row, c) = sum_col cat(row, col) C(col, c),
+// tile by tile: a tile of the concatenation is staged in shared memory, so the
+// rows of the tile can be overwritten in place once it is loaded.
 template <class T>
 __device__ void tr_apply(const Bases& B, const OpTrunc& op, const TrCat& cat, int side, int r0, int r1, int K,
-                         int k, const double* C, T* stage) {
+                         int k, const T* C, T* sC) {
   const int tid = threadIdx.x;
   const int ld = side == 0 ? op.m : op.n;
   double* out = side == 0 ? B.buf[op.U.buf] + op.U.off : B.buf[op.V.buf] + op.V.off;
-  T* so = stage + tid * TR_OUT_LD;
-  for (int base = r0; base < r1; base += blockDim.x) {
-    const int r = base + tid;
-    if (r < r1) {
-      for (int c = 0; c < k; ++c) so[c] = T(0);
-      for (int col = 0; col < K; ++col) {
-        const T v = (T)cat_value(B, op, cat, side, r, col);
-        if (v != T(0))
-          for (int c = 0; c < k; ++c) so[c] += v * (T)C[col + (int64_t)c * TR_KT];
-      }
+  const int TR = max(32, (TrCh<T>::elems / max(K, 1)) & ~31);
+  for (int t0 = r0; t0 < r1; t0 += TR) {
+    const int rows = min(TR, r1 - t0);
+    for (int e = tid; e < rows * K; e += blockDim.x) {
+      const int i = e % rows, c = e / rows;
+      sC[i + c * TR] = (T)cat_value(B, op, cat, side, t0 + i, c);
     }
     __syncthreads();
-    if (r < r1)
-      for (int c = 0; c < k; ++c) out[r + (int64_t)c * ld] = (double)so[c];
+    for (int e = tid; e < rows * k; e += blockDim.x) {
+      const int i = e % rows, c = e / rows;
+      const T* Cc = C + (int64_t)c * TR_KT;
+      T acc = T(0);
+      for (int col = 0; col < K; ++col) acc += sC[i + col * TR] * Cc[col];
+      out[(t0 + i) + (int64_t)c * ld] = (double)acc;
+    }
     __syncthreads();
   }
 }
@@ -483,7 +592,9 @@ __device__ int tr_batch(const OpTrunc& op, const TermD* tl, const int* ranks, in
     int c = kacc;
     for (int t = t0; t < t1; ++t) {
       cat.col0[t - t0] = c;
-      c += term_cols(tl[t], ranks);
+      const int kt = term_cols(tl[t], ranks);
+      for (int q = 0; q < kt && c + q < TR_KT; ++q) cat.tcol[c + q] = (unsigned char)(t - t0);
+      c += kt;
     }
     cat.col0[t1 - t0] = c;
   }
@@ -498,18 +609,17 @@ __global__ void __launch_bounds__(TR_THREADS) k_trunc(const OpTrunc* ops, int64_
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sC = reinterpret_cast<T*>(smraw);
   __shared__ TrCat cat;
-  __shared__ CoreShared cs;
+  __shared__ CoreShared<T> cs;
   __shared__ double sh[2];
   double* scr = B.scratch + (int64_t)blockIdx.x * TR_SCRATCH;
   T* Pu = reinterpret_cast<T*>(scr);
   T* Pv = reinterpret_cast<T*>(scr + TR_REG);
-  double* M = scr + 2 * TR_REG;
-  double* W = scr + 3 * TR_REG;
-  double* J = scr + 4 * TR_REG;
-  double* X = scr + TR_OFF_X;
-  double* Cu = scr + TR_OFF_CU;
-  double* Cv = scr + TR_OFF_CV;
-  T* stage = reinterpret_cast<T*>(scr + TR_OFF_STAGE);
+  T* M = reinterpret_cast<T*>(scr + 2 * TR_REG);
+  T* W = reinterpret_cast<T*>(scr + 3 * TR_REG);
+  T* J = reinterpret_cast<T*>(scr + 4 * TR_REG);
+  T* X = reinterpret_cast<T*>(scr + TR_OFF_X);
+  T* Cu = reinterpret_cast<T*>(scr + TR_OFF_CU);
+  T* Cv = reinterpret_cast<T*>(scr + TR_OFF_CV);
   for (int64_t o = blockIdx.x; o < count; o += gridDim.x) {
     const OpTrunc op = ops[o];
     const TermD* tl = terms + op.term0;
@@ -530,15 +640,24 @@ __global__ void __launch_bounds__(TR_THREADS) k_trunc(const OpTrunc* ops, int64_
         kacc = 0;
         break;
       }
+      long long tp = clock64();
+      if (B.phase && threadIdx.x == 0) {
+        atomicAdd(B.phase + 11, 1ull);
+        atomicAdd(B.phase + 12, (unsigned long long)K);
+      }
       qr_stream<T>([&](int r, int c) { return cat_value(B, op, cat, 0, r, c); }, op.m, K, Pu, sC, sh);
+      phase_mark(B.phase, 1, tp);
       qr_stream<T>([&](int r, int c) { return cat_value(B, op, cat, 1, r, c); }, op.n, K, Pv, sC, sh);
-      tr_core<T>(Pu, Pv, K, op.eps, op.kcap, M, W, J, X, Cu, Cv, cs, B.status);
+      phase_mark(B.phase, 2, tp);
+      tr_core<T>(Pu, Pv, K, op.eps, op.kcap, M, W, J, X, Cu, Cv, cs, B.status, B.phase);
+      tp = clock64();
       const int k = cs.k;
       // algorithmic flops of the batch: two streamed R factors and the apply
       if (B.flops && threadIdx.x == 0)
         atomicAdd(B.flops + OP_TRUNC, 2.0 * K * K * (double)(op.m + op.n) + 2.0 * K * (double)k * (op.m + op.n));
-      tr_apply<T>(B, op, cat, 0, 0, op.m, K, k, Cu, stage);
-      tr_apply<T>(B, op, cat, 1, 0, op.n, K, k, Cv, stage);
+      tr_apply<T>(B, op, cat, 0, 0, op.m, K, k, Cu, sC);
+      tr_apply<T>(B, op, cat, 1, 0, op.n, K, k, Cv, sC);
+      phase_mark(B.phase, 7, tp);
       kacc = k;
       __syncthreads();
     }
@@ -554,7 +673,7 @@ __global__ void __cluster_dims__(TR_CL, 1, 1) __launch_bounds__(TR_THREADS)
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sC = reinterpret_cast<T*>(smraw);
   __shared__ TrCat cat;
-  __shared__ CoreShared cs;
+  __shared__ CoreShared<T> cs;
   __shared__ double sh[2];
   cg::cluster_group cluster = cg::this_cluster();
   const int rk = (int)cluster.block_rank();
@@ -564,14 +683,13 @@ __global__ void __cluster_dims__(TR_CL, 1, 1) __launch_bounds__(TR_THREADS)
   double* scr = scr_of(rk);
   T* Pu = reinterpret_cast<T*>(scr);
   T* Pv = reinterpret_cast<T*>(scr + TR_REG);
-  double* M = scr + 2 * TR_REG;
-  double* W = scr + 3 * TR_REG;
-  double* J = scr + 4 * TR_REG;
-  double* X = scr + TR_OFF_X;
-  double* Cu0 = scr_of(0) + TR_OFF_CU;  // coefficients live with CTA 0
-  double* Cv0 = scr_of(0) + TR_OFF_CV;
+  T* M = reinterpret_cast<T*>(scr + 2 * TR_REG);
+  T* W = reinterpret_cast<T*>(scr + 3 * TR_REG);
+  T* J = reinterpret_cast<T*>(scr + 4 * TR_REG);
+  T* X = reinterpret_cast<T*>(scr + TR_OFF_X);
+  T* Cu0 = reinterpret_cast<T*>(scr_of(0) + TR_OFF_CU);  // coefficients live with CTA 0
+  T* Cv0 = reinterpret_cast<T*>(scr_of(0) + TR_OFF_CV);
   int* flag0 = reinterpret_cast<int*>(scr_of(0) + TR_OFF_FLAG);
-  T* stage = reinterpret_cast<T*>(scr + TR_OFF_STAGE);
   for (int64_t o = cid; o < count; o += ncl) {
     const OpTrunc op = ops[o];
     const TermD* tl = terms + op.term0;
@@ -602,7 +720,7 @@ __global__ void __cluster_dims__(TR_CL, 1, 1) __launch_bounds__(TR_THREADS)
       // 2. CTA 0 combines the U partials into its J region, CTA 1 the V partials
       if (rk < 2) {
         const int64_t poff = rk == 0 ? 0 : TR_REG;
-        T* fin = reinterpret_cast<T*>(J);
+        T* fin = J;
         qr_stream<T>(
             [&](int r, int c) {
               const T* P = reinterpret_cast<const T*>(scr_of(r / K) + poff);
@@ -617,7 +735,7 @@ __global__ void __cluster_dims__(TR_CL, 1, 1) __launch_bounds__(TR_THREADS)
       if (rk == 0) {
         T* Ru = Pu;
         T* Rv = Pv;
-        const T* fu = reinterpret_cast<const T*>(J);
+        const T* fu = J;
         const T* fv = reinterpret_cast<const T*>(scr_of(1) + 4 * TR_REG);
         for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
           const int i = e % K, j = e / K;
@@ -635,8 +753,8 @@ __global__ void __cluster_dims__(TR_CL, 1, 1) __launch_bounds__(TR_THREADS)
         atomicAdd(B.flops + OP_TRUNC_BIG,
                   2.0 * K * K * (double)(op.m + op.n) + 2.0 * K * (double)k * (op.m + op.n));
       // 4. all CTAs apply to their rows
-      tr_apply<T>(B, op, cat, 0, mu0, mu1, K, k, Cu0, stage);
-      tr_apply<T>(B, op, cat, 1, nv0, nv1, K, k, Cv0, stage);
+      tr_apply<T>(B, op, cat, 0, mu0, mu1, K, k, Cu0, sC);
+      tr_apply<T>(B, op, cat, 1, nv0, nv1, K, k, Cv0, sC);
       kacc = k;
       __threadfence();
       cluster.sync();

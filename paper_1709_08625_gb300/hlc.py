@@ -203,6 +203,7 @@ class Context:
         out = {"launches": int(a[0])}
         for i, name in enumerate(self.OPS):
             out[name] = {"launches": int(a[1 + 3 * i]), "ms": float(a[2 + 3 * i]), "flops": float(a[3 + 3 * i])}
+        out["persistent"] = int(a[16])
         return out
 
 

@@ -255,3 +255,41 @@ def test_serve_results_equal_standalone(hlc):
         assert done[i]["ms_total"] > 0
     alone.close()
     srv.close()
+
+
+# --------------------------------------------------------------------------
+# the persistent solve kernel: taken, and identical to wave-by-wave launches
+# --------------------------------------------------------------------------
+_SOLVE_CASE = """
+import json, sys
+sys.path.insert(0, {root!r})
+from paper_1709_08625_gb300 import hlc, inputs
+c = hlc.Context(0)
+t = c.build_tree(inputs.points(6000, 1500), leaf=64, eps=1e-6, kmax=128)
+c.counters(reset=True)
+r = t.loglik(hlc.theta(1.0, 0.05, 0.5, 1e-4), inputs.normal(6000, 1501))
+r["persistent"] = c.counters()["persistent"]
+print(json.dumps(r))
+"""
+
+
+def test_persistent_solves_match_wave_launches(hlc):
+    import json
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    runs = {}
+    for flag in ("1", "0"):
+        env = dict(os.environ, HLC_PERSISTENT=flag)
+        out = subprocess.run([sys.executable, "-c", _SOLVE_CASE.format(root=root)], env=env, capture_output=True,
+                             text=True, timeout=600)
+        assert out.returncode == 0, out.stderr[-2000:]
+        runs[flag] = json.loads(out.stdout.strip().splitlines()[-1])
+    on, off = runs["1"], runs["0"]
+    assert on["persistent"] > 0 and off["persistent"] == 0
+    # each op of a wave writes its own region, so the order in which CTAs
+    # take the ops does not change a single bit
+    for key in ("loglik", "logdet", "quad", "quad_factor", "refine_iters"):
+        assert on[key] == off[key], key
