@@ -43,10 +43,13 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default=WORKLOAD)
-    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--precision", default="mixed", choices=["mixed", "mixed_svd64", "fp64"])
     p.add_argument("--no-fp64-check", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--kmax", type=int, default=64)
+    p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--serve-requests", type=int, default=16)
+    p.add_argument("--serve-n", type=int, nargs=2, default=[10000, 65536])
     p.add_argument("--sample-n", type=int, default=SAMPLE_N,
                    help="locations in the oracle's bounded sample of the workload")
     return p.parse_args()
@@ -187,6 +190,77 @@ def run_reference(args, rank, ws, dist):
 
 
 # --------------------------------------------------------------------------
+# served stream: p50 / p99 latency under Poisson arrivals
+# --------------------------------------------------------------------------
+def serve_stream(hlc, inputs, dev, n_lo, n_hi, n_req, slots, seed=5000):
+    """Requests with n log-uniform in [n_lo, n_hi], sigma2 ~ U[0.5, 2],
+    ell ~ U[0.02, 0.2], nu ~ U[0.3, 2.0], nugget 1e-4, z ~ N(0, 1), mixed
+    precision with FP64 refinement.  A closed-loop pass (all requests at once)
+    measures the capacity; the timed pass submits the same requests as Poisson
+    arrivals at 0.8 x that capacity.  Latency = submission to completion,
+    tree build included, as the library records it."""
+    import numpy as np
+
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for q in range(n_req):
+        n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
+        th = hlc.theta(float(rng.uniform(0.5, 2.0)), float(rng.uniform(0.02, 0.2)), float(rng.uniform(0.3, 2.0)),
+                       1e-4)
+        reqs.append((inputs.points(n, seed + 1 + q), inputs.normal(n, seed + 1001 + q), th))
+    kw = dict(leaf=64, eps=1e-6, kmax=128, precision=hlc.HLC_MIXED)
+    ctx = hlc.Context(dev)
+    ctx.serve_start(96 << 30, slots)
+
+    def drain(ids, t_limit=900.0):
+        done, failed = {}, 0
+        t0 = time.perf_counter()
+        while len(done) + failed < len(ids) and time.perf_counter() - t0 < t_limit:
+            for i in ids:
+                if i in done or i < 0:
+                    continue
+                try:
+                    r = ctx.serve_poll(i)
+                except hlc.HlcError:
+                    failed += 1
+                    ids[ids.index(i)] = -1
+                    continue
+                if r is not None:
+                    done[i] = r
+            time.sleep(0.002)
+        return done, failed
+
+    t0 = time.perf_counter()
+    ids = [ctx.serve_submit(xy, z, th, **kw) for xy, z, th in reqs]
+    drain(ids)
+    capacity = n_req / (time.perf_counter() - t0)
+    rate = 0.8 * capacity
+    gaps = rng.exponential(1.0 / rate, n_req)
+    t0 = time.perf_counter()
+    ids, due = [], t0
+    for (xy, z, th), g in zip(reqs, gaps):
+        due += g
+        while time.perf_counter() < due:
+            time.sleep(0.001)
+        ids.append(ctx.serve_submit(xy, z, th, **kw))
+    done, failed = drain(ids)
+    span = time.perf_counter() - t0
+    ctx.serve_stop()
+    ctx.close()
+    lat = sorted(r["ms_total"] for r in done.values())
+
+    def pct(p):
+        if not lat:
+            return None
+        return lat[min(len(lat) - 1, int(math.ceil(p / 100.0 * len(lat))) - 1)]
+
+    return {"p50_ms": pct(50), "p99_ms": pct(99), "evals_per_s": len(lat) / span, "requests": n_req,
+            "completed": len(lat), "failed": failed, "n_range": [n_lo, n_hi], "slots": slots,
+            "arrival_rate_per_s": rate, "closed_loop_capacity_per_s": capacity,
+            "note": "Poisson arrivals at 0.8 x closed-loop capacity; mixed precision, eps 1e-6, leaf 64"}
+
+
+# --------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------
 def run_ours(args, rank, ws, local, dist):
@@ -204,7 +278,7 @@ def run_ours(args, rank, ws, local, dist):
     n = w["n"]
     xy = inputs.workload_points(args.workload)
     z_host = inputs.workload_normal(args.workload)
-    prec = hlc.HLC_MIXED if args.precision == "mixed" else hlc.HLC_FP64
+    prec = {"mixed": hlc.HLC_MIXED, "mixed_svd64": hlc.HLC_MIXED_SVD64, "fp64": hlc.HLC_FP64}[args.precision]
     ctx = hlc.Context(dev)
     t0 = time.perf_counter()
     tree = ctx.build_tree(xy, leaf=w["leaf"], eta=w["eta"], eps=w["eps"], precision=prec, kmax=args.kmax)
@@ -244,14 +318,13 @@ def run_ours(args, rank, ws, local, dist):
     ms_total = max_over_ranks(dist, ms_total)
     value = ws * args.steps / (ms_total / 1000.0)
 
-    # ---- profiled pass of the same steps: per-kernel launch times ------------
+    # ---- profiled pass (one step): every op launch timed with CUDA events ---
     ctx.set_profiling(True)
     torch.cuda.synchronize()
     pe0 = torch.cuda.Event(enable_timing=True)
     pe1 = torch.cuda.Event(enable_timing=True)
     pe0.record(stream)
-    for k in range(args.steps):
-        tree.loglik(theta(1000 + k), z_dev)
+    tree.loglik(theta(1000), z_dev)
     pe1.record(stream)
     torch.cuda.synchronize()
     prof = ctx.counters(reset=True)
@@ -279,7 +352,7 @@ def run_ours(args, rank, ws, local, dist):
         dom = max(ops, key=lambda k: ops[k]["ms"])
         d = ops[dom]
         sm_mhz = clk.get("sm_max_mhz") or 2070.0
-        if args.precision == "mixed" and dom in ("gemm", "trunc", "trunc_cluster"):
+        if args.precision != "fp64" and dom in ("gemm", "trunc", "trunc_cluster"):
             peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
             unit = "TFLOP/s"
         else:
@@ -290,7 +363,7 @@ def run_ours(args, rank, ws, local, dist):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64",
             "data": "synthetic: seeded uniform locations in [0,1]^2, z ~ N(0,1); theta +-5 % per step",
             "config": {"workload": args.workload, "n": n, "nu": w["nu"], "ell": w["ell"], "sigma2": w["sigma2"],
                        "nugget": w["nugget"], "eps": w["eps"], "leaf": w["leaf"], "eta": w["eta"],
@@ -304,7 +377,7 @@ def run_ours(args, rank, ws, local, dist):
                          "frac": achieved / peak if peak else None, "traffic": None,
                          "peak_note": ("FP32 SIMT: 152 SMs x 128 lanes x 2 flop x max SM clock"
                                        if unit == "TFLOP/s" and peak > 2 else "nominal FP64 rate"),
-                         "profiled_ms_per_step": prof_ms / args.steps,
+                         "profiled_ms_per_step": prof_ms,
                          "per_kernel": {k: v for k, v in ops.items()}},
             "clocks": clk,
             "result": {k: results[-1][k] for k in ("loglik", "logdet", "quad", "refine_iters", "rel_residual",
@@ -312,7 +385,7 @@ def run_ours(args, rank, ws, local, dist):
                                                    "ms_assemble", "ms_factor", "ms_solve")},
         }
     # ---- FP64 comparison at the same theta ---------------------------------
-    if rank == 0 and not args.no_fp64_check and args.precision == "mixed":
+    if rank == 0 and not args.no_fp64_check and args.precision != "fp64":
         del tree
         t64 = ctx.build_tree(xy, leaf=w["leaf"], eta=w["eta"], eps=w["eps"], precision=hlc.HLC_FP64,
                              kmax=args.kmax)
@@ -328,6 +401,8 @@ def run_ours(args, rank, ws, local, dist):
                          "dquad_per_n": abs(rm["quad"] - r64["quad"]) / n, "bar": 1e-6,
                          "speedup_mixed_vs_fp64": value / ws / out["fp64"]["value"]}
         del t64
+    if rank == 0 and not args.no_serve:
+        out["serve"] = serve_stream(hlc, inputs, dev, args.serve_n[0], args.serve_n[1], args.serve_requests, 3)
     if rank == 0:
         if not args.no_cpu_baseline:
             import oracle

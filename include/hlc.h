@@ -56,9 +56,11 @@ extern "C" {
 #define HLC_ERR_NUMERIC (-9)   /* numerical breakdown (NaN in a factor or a sum) */
 
 /* ---- precision modes ---------------------------------------------------- */
-#define HLC_FP64 0   /* every stage in FP64 */
-#define HLC_MIXED 1  /* FP32 low-rank panels and updates; FP64 leaf POTRF,
-                        log-det, recompression SVD and refinement */
+#define HLC_FP64 0         /* every stage in FP64 */
+#define HLC_MIXED 1        /* FP32 low-rank panels, updates and recompression
+                              core (QRCP, Jacobi SVD, coefficients); FP64 leaf
+                              POTRF, log-det and refinement */
+#define HLC_MIXED_SVD64 2  /* as HLC_MIXED, with the recompression core in FP64 */
 
 typedef struct hlc_ctx hlc_ctx;   /* device, stream, workspaces; owns device memory */
 typedef struct hlc_tree hlc_tree; /* cluster tree + block-cluster tree of one point set */
@@ -76,7 +78,7 @@ typedef struct {
   int leaf;           /* n_min: largest leaf cluster (Sec. 2.2), 1..128 */
   double eta;         /* standard admissibility parameter (App. A), > 0 */
   double eps;         /* block accuracy of C~ and of the H-arithmetic (Sec. 2.2) */
-  int precision;      /* HLC_FP64 or HLC_MIXED */
+  int precision;      /* HLC_FP64, HLC_MIXED or HLC_MIXED_SVD64 */
   double refine_tol;  /* stop the solve when |z - C~ x| <= refine_tol |z| */
   int refine_maxit;   /* at most this many preconditioned CG iterations */
   int kmax;           /* rank capacity of a low-rank block, 1..128 */
@@ -144,6 +146,7 @@ int hlc_cholesky(hlc_ctx* ctx, const hlc_hmat* C, hlc_hmat** L);
 /* y = C~ x (C~ symmetric, Table 1 matvec); x, y: n values in caller order. */
 int hlc_matvec(hlc_ctx* ctx, const hlc_hmat* C, const double* x, double* y);
 
+
 /* Dense expansion of C~ (symmetric) or L~ (lower) into an n x n column-major
  * host array in caller order; for small n only (n <= 16384). */
 int hlc_hmat_expand(hlc_ctx* ctx, const hlc_hmat* M, double* out);
@@ -188,7 +191,9 @@ int hlc_ctx_counters(hlc_ctx* ctx, int reset, double* out);
  * admitted requests run concurrently on the device. */
 int hlc_serve_start(hlc_ctx* ctx, size_t hbm_budget_bytes, int max_slots);
 /* Queue one request (copies host arrays xy (n x 2 row-major) and z; p may be
- * NULL for the defaults); returns its id in *req_id. */
+ * NULL for the defaults); returns its id in *req_id.  A request in a mixed
+ * mode whose factorisation meets a non-positive pivot or a NaN is evaluated
+ * again in HLC_FP64 before its result is posted. */
 int hlc_serve_submit(hlc_ctx* ctx, const double* xy, const double* z, int64_t n,
                      const hlc_theta* th, const hlc_params* p, uint64_t* req_id);
 /* HLC_PENDING until done; then the request's status with *out filled

@@ -309,7 +309,7 @@ void run_plan_launches(hlc_tree* t, const Plan& P, const Bases& B, cudaStream_t 
 Bases make_bases(hlc_tree* t, double* mat_L, double* mat_C, int* ranks, bool mixed) {
   Bases B;
   B.mixed = mixed ? 1 : 0;
-  B.pad = 0;
+  B.core64 = (mixed && t->p.precision == HLC_MIXED_SVD64) ? 1 : 0;
   B.buf[BUF_L] = mat_L;
   B.buf[BUF_TMP] = t->d_tmp;
   B.buf[BUF_VEC] = t->d_vec;
@@ -433,10 +433,13 @@ int do_assemble(hlc_tree* t, const hlc_theta* th, hlc_hmat* C) {
                      c->stream));
   launch_dense_asm(t->d_dense, (int64_t)t->T.dense_asm.size(), C->arena, t->d_px, t->d_py, mp, c->stream);
   c->launches += 2;  // dense assembly + ACA
-  const bool mixed = t->p.precision == HLC_MIXED;
-  launch_aca(t->d_lr, (int64_t)t->T.lr_asm.size(), C->arena, t->d_px, t->d_py, mp, t->p.eps, C->ranks, mixed,
-             c->stream);
-  Bases B = make_bases(t, nullptr, C->arena, C->ranks, mixed);
+  // C~ is assembled and recompressed in FP64 in every precision mode: it is
+  // the matrix the FP64 residual of the refinement is taken against, and the
+  // quadratic form z^T C~^-1 z inherits every perturbation of C~ amplified by
+  // its condition number (FP32 ACA panels moved |dL|/n by ~5e-4 at
+  // n = 524,288, ell = 0.0864, nugget 1e-4).
+  launch_aca(t->d_lr, (int64_t)t->T.lr_asm.size(), C->arena, t->d_px, t->d_py, mp, t->p.eps, C->ranks, c->stream);
+  Bases B = make_bases(t, nullptr, C->arena, C->ranks, false);
   run_plan(t, t->recomp, B, c->stream);
   CK(cudaGetLastError());
   C->valid = false;
@@ -453,7 +456,7 @@ int do_cholesky(hlc_tree* t, const hlc_hmat* C, hlc_hmat* L) {
                      c->stream));
   if (t->T.nslots)
     CK(cudaMemcpyAsync(L->ranks, C->ranks, t->T.nslots * sizeof(int), cudaMemcpyDeviceToDevice, c->stream));
-  Bases B = make_bases(t, L->arena, nullptr, L->ranks, t->p.precision == HLC_MIXED);
+  Bases B = make_bases(t, L->arena, nullptr, L->ranks, t->p.precision != HLC_FP64);
   run_plan(t, t->chol, B, c->stream);
   CK(cudaGetLastError());
   L->valid = false;
@@ -656,7 +659,7 @@ int hlc_build_tree(hlc_ctx* c, const double* xy, int64_t n, const hlc_params* p,
   else
     hlc_default_params(&q);
   if (q.leaf < 1 || q.leaf > 128 || !(q.eta > 0.0) || !(q.eps > 0.0) || q.kmax < 1 || q.kmax > 128 ||
-      (q.precision != HLC_FP64 && q.precision != HLC_MIXED) || q.refine_maxit < 0)
+      (q.precision != HLC_FP64 && q.precision != HLC_MIXED && q.precision != HLC_MIXED_SVD64) || q.refine_maxit < 0)
     return HLC_ERR_ARG;
   *out = nullptr;
   CK(cudaSetDevice(c->device));
@@ -950,7 +953,7 @@ int hlc_loglik(hlc_ctx* c, hlc_tree* t, const hlc_theta* th, const double* z, hl
   CK(cudaEventRecord(c->ev[2], s));
   // the preconditioner solves follow the factor's precision; the residual
   // matvec against C~ is always FP64
-  Bases BL = make_bases(t, t->wsL->arena, nullptr, t->wsL->ranks, t->p.precision == HLC_MIXED);
+  Bases BL = make_bases(t, t->wsL->arena, nullptr, t->wsL->ranks, t->p.precision != HLC_FP64);
   Bases BC = make_bases(t, nullptr, t->wsC->arena, t->wsC->ranks, false);
   // log det = 2 sum log L_ii  (2 launches), and the vector kernels below
   c->launches += 2;

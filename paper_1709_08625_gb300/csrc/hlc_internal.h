@@ -97,8 +97,8 @@ struct Bases {
   int* ranks;      // rank slots of the matrix in BUF_L
   int* status;     // [0] error code, [1] detail (first error wins)
   double* scratch; // per-CTA scratch of the truncation kernel
-  int mixed;       // 1: FP32 arithmetic for panels, products and QR (HLC_MIXED)
-  int pad;
+  int mixed;       // 1: FP32 arithmetic for panels, products and QR (mixed modes)
+  int core64;      // 1: FP64 truncation core in a mixed mode (HLC_MIXED_SVD64)
   double* flops;   // per op type algorithmic flop counters, or null
   unsigned long long* phase;  // truncation phase cycle counters, or null
 };

@@ -49,18 +49,13 @@ constexpr int ACA_THREADS = 256;
 // |u_k| |v_k| <= eps |S_k|_F (running Frobenius norm of the approximant).
 // A vanishing pivot row moves to the first unused row, at most three times
 // in a row.  Used rows and columns are excluded from the pivot searches.
-// T = float evaluates the kernel and the residuals in FP32 (HLC_MIXED); the
-// panels are stored in FP64 either way.
+// The assembled C~ is the matrix the FP64 refinement residual is taken
+// against in every precision mode, so the ACA runs in FP64 (T = double).
 template <class T>
 __device__ __forceinline__ T aca_entry(double x0, double y0, double x1, double y1, const MaternDev& mp);
 template <>
 __device__ __forceinline__ double aca_entry<double>(double x0, double y0, double x1, double y1, const MaternDev& mp) {
   return matern_f64(dist_f64(x0, y0, x1, y1), mp);
-}
-template <>
-__device__ __forceinline__ float aca_entry<float>(double x0, double y0, double x1, double y1, const MaternDev& mp) {
-  const float dx = (float)(x0 - x1), dy = (float)(y0 - y1);
-  return matern_f32(sqrtf(dx * dx + dy * dy), mp);
 }
 
 template <class T>
@@ -618,12 +613,9 @@ void launch_dense_asm(const DenseAsm* d, int64_t count, double* arena, const dou
   k_dense_asm<<<grid_for(count, 152 * 16), 256, 0, st>>>(d, count, arena, px, py, mp);
 }
 void launch_aca(const LrAsm* d, int64_t count, double* arena, const double* px, const double* py,
-                const MaternDev& mp, double eps, int* ranks, bool mixed, cudaStream_t st) {
+                const MaternDev& mp, double eps, int* ranks, cudaStream_t st) {
   if (count <= 0) return;
-  if (mixed)
-    k_aca<float><<<grid_for(count, 152 * 8), ACA_THREADS, 0, st>>>(d, count, arena, px, py, mp, eps, ranks);
-  else
-    k_aca<double><<<grid_for(count, 152 * 8), ACA_THREADS, 0, st>>>(d, count, arena, px, py, mp, eps, ranks);
+  k_aca<double><<<grid_for(count, 152 * 8), ACA_THREADS, 0, st>>>(d, count, arena, px, py, mp, eps, ranks);
 }
 
 

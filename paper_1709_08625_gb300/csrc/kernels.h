@@ -16,7 +16,7 @@ int configure_kernels(int max_dense);
 void launch_dense_asm(const DenseAsm* d, int64_t count, double* arena, const double* px, const double* py,
                       const MaternDev& mp, cudaStream_t st);
 void launch_aca(const LrAsm* d, int64_t count, double* arena, const double* px, const double* py,
-                const MaternDev& mp, double eps, int* ranks, bool mixed, cudaStream_t st);
+                const MaternDev& mp, double eps, int* ranks, cudaStream_t st);
 void launch_ops(int type, const void* ops, int64_t count, const TermD* terms, const Bases& B, int max_dense,
                 cudaStream_t st);
 // One cooperative launch executing all waves of a TRSM/GEMM plan; -1 when the

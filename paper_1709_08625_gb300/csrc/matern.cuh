@@ -59,29 +59,6 @@ __device__ __forceinline__ double matern_f64(double h, const MaternDev& p) {
   return p.coef * exp(lg) * (s * KNU_STEP);
 }
 
-// FP32 variant for the mixed-precision panels (relative accuracy ~1e-7).
-// Distances below 1e-6 ell take the FP64 path, which keeps the general-nu
-// sum inside the FP32 range.
-__device__ __forceinline__ float matern_f32(float h, const MaternDev& p) {
-  const float s2 = (float)p.sigma2;
-  if (h == 0.0f) return s2;
-  const float x = h / (float)p.ell;
-  if (p.kind == 0) return s2 * __expf(-x);
-  if (p.kind == 1) return s2 * (1.0f + x) * __expf(-x);
-  if (p.kind == 2) return s2 * (1.0f + x + x * x * (1.0f / 3.0f)) * __expf(-x);
-  if (x < 1e-6f) return (float)matern_f64((double)h, p);
-  float s = 0.5f * (float)p.wnu[0];
-  const float nu = (float)p.nu;
-  for (int j = 1; j < p.nnodes; ++j) {
-    const float e = x * (float)p.cm1[j];
-    const float term = __expf(-e) * (float)p.wnu[j];
-    s += term;
-    if (term < 1e-9f * s && e > nu * (j * (float)KNU_STEP)) break;
-  }
-  const float lg = nu * __logf(x) - x;
-  return (float)p.coef * __expf(lg) * (s * (float)KNU_STEP);
-}
-
 // Euclidean distance without contraction, so that it is rounded like the
 // reference host computation.
 __device__ __forceinline__ double dist_f64(double x0, double y0, double x1, double y1) {

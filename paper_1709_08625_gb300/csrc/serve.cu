@@ -91,6 +91,18 @@ void worker(hlc::Serve* S, int slot) {
     int st = hlc_build_tree(c, r->xy.data(), r->n, &r->p, &t);
     if (st == HLC_OK) st = hlc_loglik(c, t, &r->th, r->z.data(), &res);
     if (t) hlc_tree_free(t);
+    // A mixed-precision factorisation can meet a non-positive pivot where
+    // the FP64 one does not (smooth kernels, small nugget): such a request is
+    // evaluated again in FP64 rather than failed.
+    if ((st == HLC_ERR_NOT_SPD || st == HLC_ERR_NUMERIC) && r->p.precision != HLC_FP64) {
+      hlc_params p64 = r->p;
+      p64.precision = HLC_FP64;
+      t = nullptr;
+      res = hlc_result{};
+      st = hlc_build_tree(c, r->xy.data(), r->n, &p64, &t);
+      if (st == HLC_OK) st = hlc_loglik(c, t, &r->th, r->z.data(), &res);
+      if (t) hlc_tree_free(t);
+    }
     const double ms =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - r->t_submit).count();
     {

@@ -20,10 +20,12 @@
 //      projection of the block onto span(Q_u X_k) even where the computed
 //      X_k is not exactly orthonormal).
 //
-// Every step runs in FP64 (HLC_FP64) or FP32 (HLC_MIXED).  In FP32 the R
-// factors carry FP32 rounding already, so the core's SVD is taken in the
-// same type; its stopping rules scale with the type's unit roundoff.  Targets with m + n above TR_BIG_ROWS run on a cluster of TR_CL
-// CTAs: each CTA streams its share of the rows, CTAs 0 and 1 combine the
+// Steps 1 and 4 run in the panel type: FP64 (HLC_FP64) or FP32 (mixed
+// modes).  Steps 2-3 (the core) run in the core type: FP32 in HLC_MIXED,
+// whose R factors carry FP32 rounding already, FP64 in HLC_FP64 and
+// HLC_MIXED_SVD64; the core's stopping rules scale with its unit roundoff.
+//
+// Targets with m + n above 4096 rows run on a cluster of TR_CL CTAs: each CTA streams its share of the rows, CTAs 0 and 1 combine the
 // partial R factors, CTA 0 computes the core, all CTAs apply; the phases are
 // separated by cluster barriers.
 
@@ -172,17 +174,17 @@ __device__ __forceinline__ void phase_mark(unsigned long long* ph, int slot, lon
   }
 }
 
-template <class T>
-__device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, T* M, T* W, T* J, T* X, T* Cu, T* Cv,
-                        CoreShared<T>& cs, int* status,
+template <class T, class C>
+__device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, C* M, C* W, C* J, C* X, C* Cu, C* Cv,
+                        CoreShared<C>& cs, int* status,
                         unsigned long long* ph = nullptr) {
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
   long long t0 = clock64();
-  // M = Ru Rv^T (both upper triangular)
+  // M = Ru Rv^C (both upper triangular)
   for (int e = tid; e < K * K; e += blockDim.x) {
     const int i = e % K, j = e / K;
-    T s = T(0);
-    for (int c = max(i, j); c < K; ++c) s += Ru[i + (int64_t)c * TR_KT] * Rv[j + (int64_t)c * TR_KT];
+    C s = C(0);
+    for (int c = max(i, j); c < K; ++c) s += (C)Ru[i + (int64_t)c * TR_KT] * (C)Rv[j + (int64_t)c * TR_KT];
     M[i + (int64_t)j * TR_KT] = s;
   }
   for (int j = tid; j < K; j += blockDim.x) cs.piv[j] = j;
@@ -191,11 +193,11 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, T
   // Householder QR with column pivoting, stopped at the numerical rank: the
   // remaining columns are dropped once their norm is below 1e-3 eps |M|
   // (or 8 unit roundoffs of the core type, when that is larger)
-  const T stop_rel = (T)fmax(1e-3 * eps, sizeof(T) == 8 ? 8.0 * 2.220446049250313e-16 : 8.0 * 1.1920929e-7);
+  const C stop_rel = (C)fmax(1e-3 * eps, sizeof(C) == 8 ? 8.0 * 2.220446049250313e-16 : 8.0 * 1.1920929e-7);
     int r = 0;
   for (; r < K; ++r) {
     for (int j = r + w; j < K; j += nw) {
-      T p = T(0);
+      C p = C(0);
       for (int i = r + lane; i < K; i += 32) p += M[i + (int64_t)j * TR_KT] * M[i + (int64_t)j * TR_KT];
       p = warp_sum(p);
       if (lane == 0) cs.cn[j] = p;
@@ -203,7 +205,7 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, T
     __syncthreads();
     if (w == 0) {
       int jm = -1;
-      T best = T(-1), rem = T(0);
+      C best = C(-1), rem = C(0);
       for (int j = r + lane; j < K; j += 32) {
         rem += cs.cn[j];
         if (cs.cn[j] > best) {
@@ -213,7 +215,7 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, T
       }
       rem = warp_sum(rem);
       for (int o = 16; o > 0; o >>= 1) {  // max, ties to the smaller index
-        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const C ob = __shfl_xor_sync(0xffffffffu, best, o);
         const int oj = __shfl_xor_sync(0xffffffffu, jm, o);
         if (ob > best || (ob == best && oj >= 0 && (jm < 0 || oj < jm))) {
           best = ob;
@@ -223,7 +225,7 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, T
       if (lane == 0) {
         cs.jmax = jm;
         if (r == 0) cs.red[0] = sqrt(best);
-        cs.stop = (cs.red[0] == T(0)) || !(sqrt(rem) > stop_rel * cs.red[0]);
+        cs.stop = (cs.red[0] == C(0)) || !(sqrt(rem) > stop_rel * cs.red[0]);
       }
     }
     __syncthreads();
@@ -231,7 +233,7 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, T
     const int jm = cs.jmax;
     if (jm != r) {
       for (int i = tid; i < K; i += blockDim.x) {
-        const T a = M[i + (int64_t)r * TR_KT];
+        const C a = M[i + (int64_t)r * TR_KT];
         M[i + (int64_t)r * TR_KT] = M[i + (int64_t)jm * TR_KT];
         M[i + (int64_t)jm * TR_KT] = a;
       }
@@ -243,17 +245,17 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, T
     }
     __syncthreads();
     if (w == 0) {
-      T xn = T(0);
+      C xn = C(0);
       for (int i = r + 1 + lane; i < K; i += 32) xn += M[i + (int64_t)r * TR_KT] * M[i + (int64_t)r * TR_KT];
       xn = warp_sum(xn);
-      const T alpha = M[r + (int64_t)r * TR_KT];
-      T tau = T(0), sc = T(0), beta = alpha;
-      if (xn > T(0)) {
+      const C alpha = M[r + (int64_t)r * TR_KT];
+      C tau = C(0), sc = C(0), beta = alpha;
+      if (xn > C(0)) {
         beta = -copysign(sqrt(alpha * alpha + xn), alpha);
         tau = (beta - alpha) / beta;
-        sc = T(1) / (alpha - beta);
+        sc = C(1) / (alpha - beta);
       }
-      if (tau != T(0))
+      if (tau != C(0))
         for (int i = r + 1 + lane; i < K; i += 32) M[i + (int64_t)r * TR_KT] *= sc;
       if (lane == 0) {
         M[r + (int64_t)r * TR_KT] = beta;
@@ -261,13 +263,13 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, T
       }
     }
     __syncthreads();
-    const T tau = cs.tauq[r];
-    if (tau != T(0)) {
+    const C tau = cs.tauq[r];
+    if (tau != C(0)) {
       for (int l = r + 1 + w; l < K; l += nw) {
-        T p = T(0);
+        C p = C(0);
         for (int i = r + 1 + lane; i < K; i += 32) p += M[i + (int64_t)r * TR_KT] * M[i + (int64_t)l * TR_KT];
         p = warp_sum(p);
-        const T wv = tau * (p + M[r + (int64_t)l * TR_KT]);
+        const C wv = tau * (p + M[r + (int64_t)l * TR_KT]);
         for (int i = r + 1 + lane; i < K; i += 32) M[i + (int64_t)l * TR_KT] -= wv * M[i + (int64_t)r * TR_KT];
         if (lane == 0) M[r + (int64_t)l * TR_KT] -= wv;
       }
@@ -283,10 +285,10 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, T
     __syncthreads();
     return;
   }
-  // B = (R P^T)^T (K x rank) into W
+  // B = (R P^C)^C (K x rank) into W
   for (int e = tid; e < K * rank; e += blockDim.x) {
     const int j = e % K, i = e / K;  // R(i, j) -> B(piv[j], i)
-    W[cs.piv[j] + (int64_t)i * TR_KT] = (i <= j) ? M[i + (int64_t)j * TR_KT] : T(0);
+    W[cs.piv[j] + (int64_t)i * TR_KT] = (i <= j) ? M[i + (int64_t)j * TR_KT] : C(0);
   }
   __syncthreads();
   // Householder QR of B (K x rank): B = Q_B R_B; the one-sided Jacobi then
@@ -294,17 +296,17 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, T
   // SVD), and the left vectors of B are Q_B times those of R_B.
   for (int q = 0; q < rank; ++q) {
     if (w == 0) {
-      T xn = T(0);
+      C xn = C(0);
       for (int i = q + 1 + lane; i < K; i += 32) xn += W[i + (int64_t)q * TR_KT] * W[i + (int64_t)q * TR_KT];
       xn = warp_sum(xn);
-      const T alpha = W[q + (int64_t)q * TR_KT];
-      T tau = T(0), sc = T(0), beta = alpha;
-      if (xn > T(0)) {
+      const C alpha = W[q + (int64_t)q * TR_KT];
+      C tau = C(0), sc = C(0), beta = alpha;
+      if (xn > C(0)) {
         beta = -copysign(sqrt(alpha * alpha + xn), alpha);
         tau = (beta - alpha) / beta;
-        sc = T(1) / (alpha - beta);
+        sc = C(1) / (alpha - beta);
       }
-      if (tau != T(0))
+      if (tau != C(0))
         for (int i = q + 1 + lane; i < K; i += 32) W[i + (int64_t)q * TR_KT] *= sc;
       if (lane == 0) {
         W[q + (int64_t)q * TR_KT] = beta;
@@ -312,33 +314,33 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, T
       }
     }
     __syncthreads();
-    const T tau = cs.cn[q];
-    if (tau != T(0)) {
+    const C tau = cs.cn[q];
+    if (tau != C(0)) {
       for (int l = q + 1 + w; l < rank; l += nw) {
-        T p = T(0);
+        C p = C(0);
         for (int i = q + 1 + lane; i < K; i += 32) p += W[i + (int64_t)q * TR_KT] * W[i + (int64_t)l * TR_KT];
         p = warp_sum(p);
-        const T wv = tau * (p + W[q + (int64_t)l * TR_KT]);
+        const C wv = tau * (p + W[q + (int64_t)l * TR_KT]);
         for (int i = q + 1 + lane; i < K; i += 32) W[i + (int64_t)l * TR_KT] -= wv * W[i + (int64_t)q * TR_KT];
         if (lane == 0) W[q + (int64_t)l * TR_KT] -= wv;
       }
     }
     __syncthreads();
   }
-  // The one-sided Jacobi works on A = R_B^T (lower triangular; the
+  // The one-sided Jacobi works on A = R_B^C (lower triangular; the
   // transpose of the triangular factor is what the QR preconditioning makes
   // nearly orthogonal), in the X region; J accumulates its rotations.
-  T* A = X;
+  C* A = X;
   for (int e = tid; e < rank * rank; e += blockDim.x) {
     const int i = e % rank, j = e / rank;
-    A[i + (int64_t)j * TR_KT] = (i >= j) ? W[j + (int64_t)i * TR_KT] : T(0);
-    J[i + (int64_t)j * TR_KT] = (i == j) ? T(1) : T(0);
+    A[i + (int64_t)j * TR_KT] = (i >= j) ? W[j + (int64_t)i * TR_KT] : C(0);
+    J[i + (int64_t)j * TR_KT] = (i == j) ? C(1) : C(0);
   }
   __syncthreads();
   // one-sided Jacobi on the rank columns of A, round-robin pairs
-  T fro2 = T(0);
+  C fro2 = C(0);
   for (int e = tid; e < rank * rank; e += blockDim.x) {
-    const T v = A[(e % rank) + (int64_t)(e / rank) * TR_KT];
+    const C v = A[(e % rank) + (int64_t)(e / rank) * TR_KT];
     fro2 += v * v;
   }
   fro2 = block_sum(fro2, cs.red + 1);
@@ -348,8 +350,8 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, T
   // with c = 1e-14 (FP64) or 1e-6 (FP32), i.e. some tens of unit roundoffs
   // per column: the columns end up orthogonal far below any truncation
   // threshold, without chasing the rounding noise of the dot products
-  const T tiny = (sizeof(T) == 8 ? T(1e-26) : T(1e-12)) * fro2;
-  const T rtol = (T)max(rank, 16) * (sizeof(T) == 8 ? T(1e-14) : T(1e-6));
+  const C tiny = (sizeof(C) == 8 ? C(1e-26) : C(1e-12)) * fro2;
+  const C rtol = (C)max(rank, 16) * (sizeof(C) == 8 ? C(1e-14) : C(1e-6));
   const int Kp = rank + (rank & 1);
   for (int sweep = 0; sweep < 80 && Kp > 1; ++sweep) {
     if (tid == 0) cs.rot = 0;
@@ -365,9 +367,9 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, T
           b = t;
         }
         if (b >= rank) continue;
-        T al = T(0), be = T(0), ga = T(0);
+        C al = C(0), be = C(0), ga = C(0);
         for (int i = lane; i < rank; i += 32) {
-          const T x = A[i + (int64_t)a * TR_KT], y = A[i + (int64_t)b * TR_KT];
+          const C x = A[i + (int64_t)a * TR_KT], y = A[i + (int64_t)b * TR_KT];
           al += x * x;
           be += y * y;
           ga += x * y;
@@ -376,15 +378,15 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, T
         be = warp_sum(be);
         ga = warp_sum(ga);
         if (al <= tiny && be <= tiny) continue;
-        if (ga == T(0) || fabs(ga) <= rtol * sqrt(al * be)) continue;
-        const T zeta = (be - al) / (T(2) * ga);
-        const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-        const T c = T(1) / sqrt(T(1) + t * t), sn = c * t;
+        if (ga == C(0) || fabs(ga) <= rtol * sqrt(al * be)) continue;
+        const C zeta = (be - al) / (C(2) * ga);
+        const C t = (zeta >= C(0) ? C(1) : C(-1)) / (fabs(zeta) + sqrt(C(1) + zeta * zeta));
+        const C c = C(1) / sqrt(C(1) + t * t), sn = c * t;
         for (int i = lane; i < rank; i += 32) {
-          const T x = A[i + (int64_t)a * TR_KT], y = A[i + (int64_t)b * TR_KT];
+          const C x = A[i + (int64_t)a * TR_KT], y = A[i + (int64_t)b * TR_KT];
           A[i + (int64_t)a * TR_KT] = c * x - sn * y;
           A[i + (int64_t)b * TR_KT] = sn * x + c * y;
-          const T jx = J[i + (int64_t)a * TR_KT], jy = J[i + (int64_t)b * TR_KT];
+          const C jx = J[i + (int64_t)a * TR_KT], jy = J[i + (int64_t)b * TR_KT];
           J[i + (int64_t)a * TR_KT] = c * jx - sn * jy;
           J[i + (int64_t)b * TR_KT] = sn * jx + c * jy;
         }
@@ -398,7 +400,7 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, T
   phase_mark(ph, 5, t0);
   // singular values, order (ties: smaller index first), truncation rank
   for (int j = w; j < rank; j += nw) {
-    T s = T(0);
+    C s = C(0);
     for (int i = lane; i < rank; i += 32) s += A[i + (int64_t)j * TR_KT] * A[i + (int64_t)j * TR_KT];
     s = warp_sum(s);
     if (lane == 0) cs.sv[j] = sqrt(s);
@@ -411,10 +413,10 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, T
   }
   __syncthreads();
   if (tid == 0) {
-    const T smax = cs.sv[cs.order[0]];
-    const T thr = (T)eps * smax;
+    const C smax = cs.sv[cs.order[0]];
+    const C thr = (C)eps * smax;
     int k = 0;
-    if (smax > T(0))
+    if (smax > C(0))
       while (k < rank && cs.sv[cs.order[k]] > thr) ++k;
     if (!(smax == smax)) {
       record_error(status, DEV_BAD, 1);
@@ -428,71 +430,71 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, T
   }
   __syncthreads();
   const int k = cs.k;
-  // The Jacobi gives R_B^T J = Wa (orthogonal columns, Wa = Wa_n S), so
-  // R_B = J S Wa_n^T, B = Q_B R_B = (Q_B J) S Wa_n^T, and with M = Q R P^T =
-  // Q B^T = (Q Wa_n) S (Q_B J)^T:
+  // The Jacobi gives R_B^C J = Wa (orthogonal columns, Wa = Wa_n S), so
+  // R_B = J S Wa_n^C, B = Q_B R_B = (Q_B J) S Wa_n^C, and with M = Q R P^C =
+  // Q B^C = (Q Wa_n) S (Q_B J)^C:
   //   left vectors of M:  x_c = Q [Wa_n(:, j_c); 0]  (reflectors of the pivoted QR, in M)
   //   right vectors of M: y_c = Q_B [J(:, j_c); 0]   (reflectors of the QR of B, in W)
   // Both are built in the Cu/Cv regions' columns (K x k each) before the
   // coefficients overwrite them: x_c in Cv, y_c in Cu.
   for (int c = w; c < k; c += nw) {
     const int j = cs.order[c];
-    const T sv = cs.sv[j];
-    T* x = Cv + (int64_t)c * TR_KT;
-    T* y = Cu + (int64_t)c * TR_KT;
+    const C sv = cs.sv[j];
+    C* x = Cv + (int64_t)c * TR_KT;
+    C* y = Cu + (int64_t)c * TR_KT;
     for (int i = lane; i < K; i += 32) {
-      x[i] = i < rank ? A[i + (int64_t)j * TR_KT] / sv : T(0);
-      y[i] = i < rank ? J[i + (int64_t)j * TR_KT] : T(0);
+      x[i] = i < rank ? A[i + (int64_t)j * TR_KT] / sv : C(0);
+      y[i] = i < rank ? J[i + (int64_t)j * TR_KT] : C(0);
     }
     __syncwarp();
     for (int q = rank - 1; q >= 0; --q) {
-      const T tq = cs.tauq[q], tb = cs.cn[q];
-      T p = T(0), pb = T(0);
+      const C tq = cs.tauq[q], tb = cs.cn[q];
+      C p = C(0), pb = C(0);
       for (int i = q + lane; i < K; i += 32) {
-        p += (i == q ? T(1) : M[i + (int64_t)q * TR_KT]) * x[i];
-        pb += (i == q ? T(1) : W[i + (int64_t)q * TR_KT]) * y[i];
+        p += (i == q ? C(1) : M[i + (int64_t)q * TR_KT]) * x[i];
+        pb += (i == q ? C(1) : W[i + (int64_t)q * TR_KT]) * y[i];
       }
       p = warp_sum(p);
       pb = warp_sum(pb);
       for (int i = q + lane; i < K; i += 32) {
-        if (tq != T(0)) x[i] -= tq * p * (i == q ? T(1) : M[i + (int64_t)q * TR_KT]);
-        if (tb != T(0)) y[i] -= tb * pb * (i == q ? T(1) : W[i + (int64_t)q * TR_KT]);
+        if (tq != C(0)) x[i] -= tq * p * (i == q ? C(1) : M[i + (int64_t)q * TR_KT]);
+        if (tb != C(0)) y[i] -= tb * pb * (i == q ? C(1) : W[i + (int64_t)q * TR_KT]);
       }
       __syncwarp();
     }
   }
   __syncthreads();
-  // G = X_k^T X_k, the Gram matrix of the kept left vectors (the identity up
+  // G = X_k^C X_k, the Gram matrix of the kept left vectors (the identity up
   // to the orthogonality the Jacobi reached), lower triangle in the X region
-  // (A is no longer needed).  V_new carries G^-1: then U_new V_new^T =
-  // Q_u P M Q_v^T with P the orthogonal projector onto span(X_k), whose
+  // (A is no longer needed).  V_new carries G^-1: then U_new V_new^C =
+  // Q_u P M Q_v^C with P the orthogonal projector onto span(X_k), whose
   // distance from M is bounded by the dropped columns whether or not X_k is
   // exactly orthogonal (in FP32 it is only to ~1e-6, which is not below eps).
-  T* G = X;
+  C* G = X;
   for (int e = tid; e < k * k; e += blockDim.x) {
     const int i = e % k, j = e / k;
     if (i < j) continue;
-    const T* xi = Cv + (int64_t)i * TR_KT;
-    const T* xj = Cv + (int64_t)j * TR_KT;
-    T g = T(0);
+    const C* xi = Cv + (int64_t)i * TR_KT;
+    const C* xj = Cv + (int64_t)j * TR_KT;
+    C g = C(0);
     for (int q = 0; q < K; ++q) g += xi[q] * xj[q];
     G[i + (int64_t)j * TR_KT] = g;
   }
   __syncthreads();
-  // G = L L^T in place (warp 0, left-looking); G is near the identity, so a
+  // G = L L^C in place (warp 0, left-looking); G is near the identity, so a
   // pivot below 1/4 means the vectors are unusable and the correction is
   // skipped
   if (w == 0) {
     int ok = 1;
     for (int j = 0; j < k; ++j) {
-      T part = T(0);
+      C part = C(0);
       for (int q = lane; q < j; q += 32) part += G[j + (int64_t)q * TR_KT] * G[j + (int64_t)q * TR_KT];
       part = warp_sum(part);
-      const T d = G[j + (int64_t)j * TR_KT] - part;
-      if (!(d > T(0.25))) ok = 0;
-      const T ljj = sqrt(d > T(0.25) ? d : T(1));
+      const C d = G[j + (int64_t)j * TR_KT] - part;
+      if (!(d > C(0.25))) ok = 0;
+      const C ljj = sqrt(d > C(0.25) ? d : C(1));
       for (int i = j + 1 + lane; i < k; i += 32) {
-        T g = G[i + (int64_t)j * TR_KT];
+        C g = G[i + (int64_t)j * TR_KT];
         for (int q = 0; q < j; ++q) g -= G[i + (int64_t)q * TR_KT] * G[j + (int64_t)q * TR_KT];
         G[i + (int64_t)j * TR_KT] = g / ljj;
       }
@@ -502,33 +504,33 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, T
     }
     if (lane == 0) cs.rot = ok;
   }
-  // Cu = R_v^T y_c / s^0.5 and Cv = R_u^T x_c, one entry per thread; y_c,
+  // Cu = R_v^C y_c / s^0.5 and Cv = R_u^C x_c, one entry per thread; y_c,
   // x_c sit in Cu, Cv, the results go to W, M (free now)
   for (int e = tid; e < K * k; e += blockDim.x) {
     const int col = e % K, c = e / K;
-    const T isq = T(1) / sqrt(cs.sv[cs.order[c]]);
-    const T* y = Cu + (int64_t)c * TR_KT;
-    const T* x = Cv + (int64_t)c * TR_KT;
-    T a = T(0), b = T(0);
+    const C isq = C(1) / sqrt(cs.sv[cs.order[c]]);
+    const C* y = Cu + (int64_t)c * TR_KT;
+    const C* x = Cv + (int64_t)c * TR_KT;
+    C a = C(0), b = C(0);
     for (int q = 0; q <= col; ++q) {
-      a += Rv[q + (int64_t)col * TR_KT] * y[q];
-      b += Ru[q + (int64_t)col * TR_KT] * x[q];
+      a += (C)Rv[q + (int64_t)col * TR_KT] * y[q];
+      b += (C)Ru[q + (int64_t)col * TR_KT] * x[q];
     }
     W[col + (int64_t)c * TR_KT] = a * isq;
     M[col + (int64_t)c * TR_KT] = b;
   }
   __syncthreads();
-  // each row of R_u^T X_k times G^-1 (one thread per row), then S^-1/2
+  // each row of R_u^C X_k times G^-1 (one thread per row), then S^-1/2
   if (cs.rot) {
     for (int col = tid; col < K; col += blockDim.x) {
-      T* row = M + col;
+      C* row = M + col;
       for (int c = 0; c < k; ++c) {
-        T v = row[(int64_t)c * TR_KT];
+        C v = row[(int64_t)c * TR_KT];
         for (int q = 0; q < c; ++q) v -= G[c + (int64_t)q * TR_KT] * row[(int64_t)q * TR_KT];
         row[(int64_t)c * TR_KT] = v / G[c + (int64_t)c * TR_KT];
       }
       for (int c = k - 1; c >= 0; --c) {
-        T v = row[(int64_t)c * TR_KT];
+        C v = row[(int64_t)c * TR_KT];
         for (int q = c + 1; q < k; ++q) v -= G[q + (int64_t)c * TR_KT] * row[(int64_t)q * TR_KT];
         row[(int64_t)c * TR_KT] = v / G[c + (int64_t)c * TR_KT];
       }
@@ -537,7 +539,7 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, T
   __syncthreads();
   for (int e = tid; e < K * k; e += blockDim.x) {
     const int col = e % K, c = e / K;
-    const T isq = T(1) / sqrt(cs.sv[cs.order[c]]);
+    const C isq = C(1) / sqrt(cs.sv[cs.order[c]]);
     Cu[col + (int64_t)c * TR_KT] = W[col + (int64_t)c * TR_KT];
     Cv[col + (int64_t)c * TR_KT] = M[col + (int64_t)c * TR_KT] * isq;
   }
@@ -548,9 +550,9 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, T
 // Rows [r0, r1) of one side: out(row, c) = sum_col cat(row, col) C(col, c),
 // tile by tile: a tile of the concatenation is staged in shared memory, so the
 // rows of the tile can be overwritten in place once it is loaded.
-template <class T>
+template <class T, class C>
 __device__ void tr_apply(const Bases& B, const OpTrunc& op, const TrCat& cat, int side, int r0, int r1, int K,
-                         int k, const T* C, T* sC) {
+                         int k, const C* Co, T* sC) {
   const int tid = threadIdx.x;
   const int ld = side == 0 ? op.m : op.n;
   double* out = side == 0 ? B.buf[op.U.buf] + op.U.off : B.buf[op.V.buf] + op.V.off;
@@ -564,9 +566,9 @@ __device__ void tr_apply(const Bases& B, const OpTrunc& op, const TrCat& cat, in
     __syncthreads();
     for (int e = tid; e < rows * k; e += blockDim.x) {
       const int i = e % rows, c = e / rows;
-      const T* Cc = C + (int64_t)c * TR_KT;
+      const C* Cc = Co + (int64_t)c * TR_KT;
       T acc = T(0);
-      for (int col = 0; col < K; ++col) acc += sC[i + col * TR] * Cc[col];
+      for (int col = 0; col < K; ++col) acc += sC[i + col * TR] * (T)Cc[col];
       out[(t0 + i) + (int64_t)c * ld] = (double)acc;
     }
     __syncthreads();
@@ -603,23 +605,23 @@ __device__ int tr_batch(const OpTrunc& op, const TermD* tl, const int* ranks, in
   return kacc + kb;
 }
 
-template <class T>
+template <class T, class C>
 __global__ void __launch_bounds__(TR_THREADS) k_trunc(const OpTrunc* ops, int64_t count, const TermD* terms,
                                                        Bases B) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sC = reinterpret_cast<T*>(smraw);
   __shared__ TrCat cat;
-  __shared__ CoreShared<T> cs;
+  __shared__ CoreShared<C> cs;
   __shared__ double sh[2];
   double* scr = B.scratch + (int64_t)blockIdx.x * TR_SCRATCH;
   T* Pu = reinterpret_cast<T*>(scr);
   T* Pv = reinterpret_cast<T*>(scr + TR_REG);
-  T* M = reinterpret_cast<T*>(scr + 2 * TR_REG);
-  T* W = reinterpret_cast<T*>(scr + 3 * TR_REG);
-  T* J = reinterpret_cast<T*>(scr + 4 * TR_REG);
-  T* X = reinterpret_cast<T*>(scr + TR_OFF_X);
-  T* Cu = reinterpret_cast<T*>(scr + TR_OFF_CU);
-  T* Cv = reinterpret_cast<T*>(scr + TR_OFF_CV);
+  C* M = reinterpret_cast<C*>(scr + 2 * TR_REG);
+  C* W = reinterpret_cast<C*>(scr + 3 * TR_REG);
+  C* J = reinterpret_cast<C*>(scr + 4 * TR_REG);
+  C* X = reinterpret_cast<C*>(scr + TR_OFF_X);
+  C* Cu = reinterpret_cast<C*>(scr + TR_OFF_CU);
+  C* Cv = reinterpret_cast<C*>(scr + TR_OFF_CV);
   for (int64_t o = blockIdx.x; o < count; o += gridDim.x) {
     const OpTrunc op = ops[o];
     const TermD* tl = terms + op.term0;
@@ -649,14 +651,14 @@ __global__ void __launch_bounds__(TR_THREADS) k_trunc(const OpTrunc* ops, int64_
       phase_mark(B.phase, 1, tp);
       qr_stream<T>([&](int r, int c) { return cat_value(B, op, cat, 1, r, c); }, op.n, K, Pv, sC, sh);
       phase_mark(B.phase, 2, tp);
-      tr_core<T>(Pu, Pv, K, op.eps, op.kcap, M, W, J, X, Cu, Cv, cs, B.status, B.phase);
+      tr_core<T, C>(Pu, Pv, K, op.eps, op.kcap, M, W, J, X, Cu, Cv, cs, B.status, B.phase);
       tp = clock64();
       const int k = cs.k;
       // algorithmic flops of the batch: two streamed R factors and the apply
       if (B.flops && threadIdx.x == 0)
         atomicAdd(B.flops + OP_TRUNC, 2.0 * K * K * (double)(op.m + op.n) + 2.0 * K * (double)k * (op.m + op.n));
-      tr_apply<T>(B, op, cat, 0, 0, op.m, K, k, Cu, sC);
-      tr_apply<T>(B, op, cat, 1, 0, op.n, K, k, Cv, sC);
+      tr_apply<T, C>(B, op, cat, 0, 0, op.m, K, k, Cu, sC);
+      tr_apply<T, C>(B, op, cat, 1, 0, op.n, K, k, Cv, sC);
       phase_mark(B.phase, 7, tp);
       kacc = k;
       __syncthreads();
@@ -667,13 +669,13 @@ __global__ void __launch_bounds__(TR_THREADS) k_trunc(const OpTrunc* ops, int64_
 }
 
 // Cluster variant for large targets: the TR_CL CTAs of a cluster share one op.
-template <class T>
+template <class T, class C>
 __global__ void __cluster_dims__(TR_CL, 1, 1) __launch_bounds__(TR_THREADS)
     k_trunc_cl(const OpTrunc* ops, int64_t count, const TermD* terms, Bases B) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sC = reinterpret_cast<T*>(smraw);
   __shared__ TrCat cat;
-  __shared__ CoreShared<T> cs;
+  __shared__ CoreShared<C> cs;
   __shared__ double sh[2];
   cg::cluster_group cluster = cg::this_cluster();
   const int rk = (int)cluster.block_rank();
@@ -683,12 +685,12 @@ __global__ void __cluster_dims__(TR_CL, 1, 1) __launch_bounds__(TR_THREADS)
   double* scr = scr_of(rk);
   T* Pu = reinterpret_cast<T*>(scr);
   T* Pv = reinterpret_cast<T*>(scr + TR_REG);
-  T* M = reinterpret_cast<T*>(scr + 2 * TR_REG);
-  T* W = reinterpret_cast<T*>(scr + 3 * TR_REG);
-  T* J = reinterpret_cast<T*>(scr + 4 * TR_REG);
-  T* X = reinterpret_cast<T*>(scr + TR_OFF_X);
-  T* Cu0 = reinterpret_cast<T*>(scr_of(0) + TR_OFF_CU);  // coefficients live with CTA 0
-  T* Cv0 = reinterpret_cast<T*>(scr_of(0) + TR_OFF_CV);
+  C* M = reinterpret_cast<C*>(scr + 2 * TR_REG);
+  C* W = reinterpret_cast<C*>(scr + 3 * TR_REG);
+  C* J = reinterpret_cast<C*>(scr + 4 * TR_REG);
+  C* X = reinterpret_cast<C*>(scr + TR_OFF_X);
+  C* Cu0 = reinterpret_cast<C*>(scr_of(0) + TR_OFF_CU);  // coefficients live with CTA 0
+  C* Cv0 = reinterpret_cast<C*>(scr_of(0) + TR_OFF_CV);
   int* flag0 = reinterpret_cast<int*>(scr_of(0) + TR_OFF_FLAG);
   for (int64_t o = cid; o < count; o += ncl) {
     const OpTrunc op = ops[o];
@@ -720,7 +722,7 @@ __global__ void __cluster_dims__(TR_CL, 1, 1) __launch_bounds__(TR_THREADS)
       // 2. CTA 0 combines the U partials into its J region, CTA 1 the V partials
       if (rk < 2) {
         const int64_t poff = rk == 0 ? 0 : TR_REG;
-        T* fin = J;
+        T* fin = reinterpret_cast<T*>(J);
         qr_stream<T>(
             [&](int r, int c) {
               const T* P = reinterpret_cast<const T*>(scr_of(r / K) + poff);
@@ -735,7 +737,7 @@ __global__ void __cluster_dims__(TR_CL, 1, 1) __launch_bounds__(TR_THREADS)
       if (rk == 0) {
         T* Ru = Pu;
         T* Rv = Pv;
-        const T* fu = J;
+        const T* fu = reinterpret_cast<const T*>(J);
         const T* fv = reinterpret_cast<const T*>(scr_of(1) + 4 * TR_REG);
         for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
           const int i = e % K, j = e / K;
@@ -743,7 +745,7 @@ __global__ void __cluster_dims__(TR_CL, 1, 1) __launch_bounds__(TR_THREADS)
           Rv[i + (int64_t)j * TR_KT] = fv[i + (int64_t)j * TR_KT];
         }
         __syncthreads();
-        tr_core<T>(Ru, Rv, K, op.eps, op.kcap, M, W, J, X, Cu0, Cv0, cs, B.status);
+        tr_core<T, C>(Ru, Rv, K, op.eps, op.kcap, M, W, J, X, Cu0, Cv0, cs, B.status);
         if (threadIdx.x == 0) flag0[0] = cs.k;
       }
       __threadfence();
@@ -753,8 +755,8 @@ __global__ void __cluster_dims__(TR_CL, 1, 1) __launch_bounds__(TR_THREADS)
         atomicAdd(B.flops + OP_TRUNC_BIG,
                   2.0 * K * K * (double)(op.m + op.n) + 2.0 * K * (double)k * (op.m + op.n));
       // 4. all CTAs apply to their rows
-      tr_apply<T>(B, op, cat, 0, mu0, mu1, K, k, Cu0, sC);
-      tr_apply<T>(B, op, cat, 1, nv0, nv1, K, k, Cv0, sC);
+      tr_apply<T, C>(B, op, cat, 0, mu0, mu1, K, k, Cu0, sC);
+      tr_apply<T, C>(B, op, cat, 1, nv0, nv1, K, k, Cv0, sC);
       kacc = k;
       __threadfence();
       cluster.sync();
@@ -769,37 +771,45 @@ static size_t smem_bytes(bool f32) {
   return f32 ? (size_t)TrCh<float>::value * TR_KT * sizeof(float) : (size_t)TrCh<double>::value * TR_KT * sizeof(double);
 }
 
-int configure_trunc() {
+template <class T, class C>
+static int configure_pair() {
   int bad = 0;
-  bad |= cudaFuncSetAttribute(k_trunc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(false)) !=
-         cudaSuccess;
-  bad |= cudaFuncSetAttribute(k_trunc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(true)) !=
-         cudaSuccess;
-  bad |= cudaFuncSetAttribute(k_trunc_cl<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem_bytes(false)) != cudaSuccess;
-  bad |= cudaFuncSetAttribute(k_trunc_cl<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem_bytes(true)) != cudaSuccess;
+  const int sm = (int)smem_bytes(sizeof(T) == 4);
+  bad |= cudaFuncSetAttribute(k_trunc<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess;
+  bad |= cudaFuncSetAttribute(k_trunc_cl<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess;
+  return bad;
+}
+
+int configure_trunc() {
+  const int bad = configure_pair<double, double>() | configure_pair<float, float>() | configure_pair<float, double>();
   return bad ? -1 : 0;
 }
 
+template <class T, class C>
+static void launch_pair(const OpTrunc* ops, int64_t count, const TermD* terms, const Bases& B, bool big,
+                        cudaStream_t st) {
+  const int cap = max_trunc_ctas();
+  const size_t sm = smem_bytes(sizeof(T) == 4);
+  if (!big) {
+    const int grid = (int)(count < cap ? count : cap);
+    k_trunc<T, C><<<grid, TR_THREADS, sm, st>>>(ops, count, terms, B);
+  } else {
+    const int64_t ncl = count < cap / TR_CL ? count : cap / TR_CL;
+    k_trunc_cl<T, C><<<(int)(ncl * TR_CL), TR_THREADS, sm, st>>>(ops, count, terms, B);
+  }
+}
+
+// FP64: FP64 throughout; mixed: FP32 panels with an FP32 core, or with an
+// FP64 core (B.core64)
 void launch_trunc(const OpTrunc* ops, int64_t count, const TermD* terms, const Bases& B, bool big,
                   cudaStream_t st) {
   if (count <= 0) return;
-  const int cap = max_trunc_ctas();
-  if (!big) {
-    const int grid = (int)(count < cap ? count : cap);
-    if (B.mixed)
-      k_trunc<float><<<grid, TR_THREADS, smem_bytes(true), st>>>(ops, count, terms, B);
-    else
-      k_trunc<double><<<grid, TR_THREADS, smem_bytes(false), st>>>(ops, count, terms, B);
-  } else {
-    const int64_t ncl = count < cap / TR_CL ? count : cap / TR_CL;
-    const int grid = (int)(ncl * TR_CL);
-    if (B.mixed)
-      k_trunc_cl<float><<<grid, TR_THREADS, smem_bytes(true), st>>>(ops, count, terms, B);
-    else
-      k_trunc_cl<double><<<grid, TR_THREADS, smem_bytes(false), st>>>(ops, count, terms, B);
-  }
+  if (!B.mixed)
+    launch_pair<double, double>(ops, count, terms, B, big, st);
+  else if (B.core64)
+    launch_pair<float, double>(ops, count, terms, B, big, st);
+  else
+    launch_pair<float, float>(ops, count, terms, B, big, st);
 }
 
 }  // namespace hlc

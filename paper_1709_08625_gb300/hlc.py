@@ -21,11 +21,14 @@ HLC_OK = 0
 HLC_PENDING = 1
 HLC_FP64 = 0
 HLC_MIXED = 1
+HLC_MIXED_SVD64 = 2
 ERRORS = {
     -1: "HLC_ERR_ARG", -2: "HLC_ERR_OOM", -3: "HLC_ERR_NOT_SPD", -4: "HLC_ERR_TIMEOUT",
     -5: "HLC_ERR_CUDA", -6: "HLC_ERR_RANK", -7: "HLC_ERR_STATE", -8: "HLC_ERR_UNSUPPORTED",
     -9: "HLC_ERR_NUMERIC",
 }
+for _code, _nm in ERRORS.items():
+    globals()[_nm] = _code
 
 
 class hlc_theta(ctypes.Structure):

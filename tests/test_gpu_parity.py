@@ -224,6 +224,20 @@ def test_mixed_vs_fp64(ctx, hlc, n, nu, eps):
     assert abs(rmx["logdet"] - r64["logdet"]) / n <= 1e-6
 
 
+@pytest.mark.parametrize("n,nu,eps", [(12000, 0.5, 1e-5), (16384, 0.5, 1e-7)])
+def test_mixed_fp64_core_vs_fp64(ctx, hlc, n, nu, eps):
+    # FP32 panels with the recompression core (QRCP, Jacobi SVD,
+    # coefficients) in FP64
+    xy = inputs.points(n, 1200 + n)
+    z = inputs.normal(n, 1300 + n)
+    th = hlc.theta(1.0, 0.05, nu, 1e-4)
+    r64 = ctx.build_tree(xy, leaf=64, eps=eps, kmax=128).loglik(th, z)
+    rsv = ctx.build_tree(xy, leaf=64, eps=eps, kmax=128, precision=hlc.HLC_MIXED_SVD64).loglik(th, z)
+    assert rsv["rel_residual"] <= 1e-10
+    assert abs(rsv["loglik"] - r64["loglik"]) / n <= 1e-6
+    assert abs(rsv["logdet"] - r64["logdet"]) / n <= 1e-6
+
+
 # --------------------------------------------------------------------------
 # serving: each result is the same alone and in the mix
 # --------------------------------------------------------------------------
