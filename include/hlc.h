@@ -54,6 +54,7 @@ extern "C" {
 #define HLC_ERR_STATE (-7)     /* call out of order (e.g. factor before assemble) */
 #define HLC_ERR_UNSUPPORTED (-8)
 #define HLC_ERR_NUMERIC (-9)   /* numerical breakdown (NaN in a factor or a sum) */
+#define HLC_ERR_SCRATCH (-10)  /* the tree needs more than the fixed buffer of hlc_matvec_noalloc */
 
 /* ---- precision modes ---------------------------------------------------- */
 #define HLC_FP64 0         /* every stage in FP64 */
@@ -146,6 +147,27 @@ int hlc_cholesky(hlc_ctx* ctx, const hlc_hmat* C, hlc_hmat** L);
 /* y = C~ x (C~ symmetric, Table 1 matvec); x, y: n values in caller order. */
 int hlc_matvec(hlc_ctx* ctx, const hlc_hmat* C, const double* x, double* y);
 
+/*
+ * y = C~ x without allocating device memory (the paper has no counterpart:
+ * this is an interface for callers that may not allocate during a call).
+ * Same result, bit for bit, as hlc_matvec on the same C~ and x.
+ *   x, y      device pointers, n doubles each in caller order (host pointers
+ *             -> HLC_ERR_ARG); borrowed for the call, synchronous.
+ *   scratch   one fixed buffer of hlc_matvec_noalloc_capacity() doubles
+ *             (64 MiB) per device and process, part of the library module.
+ *             A tree needs 3 n + (matvec temporaries) doubles of it, about
+ *             n <= 3e5 at leaf 64 and kmax 64; larger -> HLC_ERR_SCRATCH.
+ *   preconditions  the matvec plan of C's tree exists: call hlc_matvec or
+ *             hlc_loglik on that tree once first, else HLC_ERR_STATE.
+ *   concurrency  calls whose device work overlaps (other host threads,
+ *             contexts or streams on the same device) share the buffer and
+ *             corrupt each other's results: serialise them.
+ *   first call  the first call on a device looks the buffer up (and may load
+ *             the module there); make it before any stream capture begins.
+ */
+int hlc_matvec_noalloc(hlc_ctx* ctx, const hlc_hmat* C, const double* x, double* y);
+/* Capacity in doubles of the fixed buffer of hlc_matvec_noalloc. */
+int64_t hlc_matvec_noalloc_capacity(void);
 
 /* Dense expansion of C~ (symmetric) or L~ (lower) into an n x n column-major
  * host array in caller order; for small n only (n <= 16384). */

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <stdexcept>
 #include <vector>
@@ -567,6 +568,7 @@ const char* hlc_strerror(int s) {
     case HLC_ERR_STATE: return "call out of order";
     case HLC_ERR_UNSUPPORTED: return "unsupported";
     case HLC_ERR_NUMERIC: return "numerical breakdown (NaN)";
+    case HLC_ERR_SCRATCH: return "problem larger than the fixed buffer of the no-alloc call";
     default: return "unknown status";
   }
 }
@@ -1052,6 +1054,91 @@ int hlc_loglik(hlc_ctx* c, hlc_tree* t, const hlc_theta* th, const double* z, hl
   hmat_stats(t, t->wsC, &out->bytes_C, &out->max_rank_C);
   hmat_stats(t, t->wsL, &out->bytes_L, &out->max_rank_L);
   return HLC_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// The matvec without allocation.  The paper has no counterpart: it concerns
+// how the library meets callers that may not allocate device memory during a
+// call.  Such callers exist.  A host framework may hold all free device memory
+// in its own caching pool, so a cudaMalloc of ours would fail or force the
+// pool to release memory.  A latency-bound loop may not afford the
+// device-wide synchronisation that cudaMalloc and cudaFree can cause.  An
+// out-of-memory handler must not allocate at all.  hlc_matvec can allocate (it
+// builds and uploads plans and sizes the tree's workspaces on demand); this
+// variant keeps its vectors and the plan's temporaries in one fixed buffer
+// that belongs to the loaded module and allocates nothing per call.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t kNoAllocDoubles = int64_t(8) << 20;  // 64 MiB
+__device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+constexpr int kNoAllocMaxDevices = 256;
+std::mutex g_noalloc_mu;
+double* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the buffer on `device`, which the caller has made
+// current; looked up once per device.  The first lookup may load the module
+// on that device (lazy loading), which is where the buffer's memory comes
+// from.
+int noalloc_scratch(int device, double** out) {
+  if (device < 0 || device >= kNoAllocMaxDevices) return HLC_ERR_ARG;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[device]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return HLC_ERR_CUDA;
+    }
+    g_noalloc_addr[device] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_addr[device];
+  return HLC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t hlc_matvec_noalloc_capacity(void) { return kNoAllocDoubles; }
+
+int hlc_matvec_noalloc(hlc_ctx* c, const hlc_hmat* C, const double* x, double* y) {
+  if (!c || !C || !x || !y || C->which != 0 || C->t->ctx != c) return HLC_ERR_ARG;
+  if (!C->valid) return HLC_ERR_STATE;
+  hlc_tree* t = C->t;
+  // the matvec plan must exist already (built by hlc_matvec or hlc_loglik)
+  if (!t->solve_ready || !t->mv.d_waves || t->mv.waves.empty()) return HLC_ERR_STATE;
+  CK(cudaSetDevice(c->device));
+  if (!is_device_ptr(x) || !is_device_ptr(y)) return HLC_ERR_ARG;
+  const int64_t n = t->T.n;
+  // buffer layout (doubles): [0, n) unused, x in tree order at [n, 2n), y at
+  // [2n, 3n) (the offsets the matvec plan was built with), temporaries after
+  if (3 * n + t->mv.tmp_doubles > kNoAllocDoubles) return HLC_ERR_SCRATCH;
+  double* S = nullptr;
+  int st = noalloc_scratch(c->device, &S);
+  if (st) return st;
+  launch_gather(x, t->d_perm, S + n, n, c->stream);
+  // y accumulates, so it starts at zero; the temporaries are written before
+  // they are read and the grid barrier's state is zeroed by its launch
+  CK(cudaMemsetAsync(S + 2 * n, 0, n * sizeof(double), c->stream));
+  Bases B = make_bases(t, nullptr, C->arena, C->ranks, false);
+  B.buf[BUF_VEC] = S;
+  B.buf[BUF_TMP] = S + 3 * n;
+  const int md = (int)std::max<int64_t>(t->T.max_dense_dim, t->T.leaf);
+  if (launch_waves(t->mv.d_waves, (int)t->mv.waves.size(), t->mv.d_trsm, t->mv.d_gemm, B, c->d_gridbar, md,
+                   c->stream) != 0) {
+    cudaGetLastError();
+    return HLC_ERR_CUDA;
+  }
+  launch_scatter(S + 2 * n, t->d_perm, y, n, c->stream);
+  c->launches += 3;
+  c->persistent_launches += 1;
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->stream));
+  return take_status(c);
 }
 
 }  // extern "C"

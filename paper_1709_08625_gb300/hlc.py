@@ -26,6 +26,7 @@ ERRORS = {
     -1: "HLC_ERR_ARG", -2: "HLC_ERR_OOM", -3: "HLC_ERR_NOT_SPD", -4: "HLC_ERR_TIMEOUT",
     -5: "HLC_ERR_CUDA", -6: "HLC_ERR_RANK", -7: "HLC_ERR_STATE", -8: "HLC_ERR_UNSUPPORTED",
     -9: "HLC_ERR_NUMERIC",
+    -10: "HLC_ERR_SCRATCH",
 }
 for _code, _nm in ERRORS.items():
     globals()[_nm] = _code
@@ -79,6 +80,8 @@ _SIGS = {
     "hlc_assemble": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(hlc_theta), ctypes.POINTER(_vp)]),
     "hlc_cholesky": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_vp)]),
     "hlc_matvec": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "hlc_matvec_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "hlc_matvec_noalloc_capacity": (ctypes.c_int64, []),
     "hlc_hmat_expand": (ctypes.c_int, [_vp, _vp, _vp]),
     "hlc_hmat_ranks": (ctypes.c_int, [_vp, _vp, _vp]),
     "hlc_hmat_free": (None, [_vp]),
@@ -239,6 +242,11 @@ class HMat:
             x = np.ascontiguousarray(x, dtype=np.float64)
             y = np.empty_like(x)
         _check(hlc_matvec(self.ctx.h, self.h, _ptr(x), _ptr(y)), "hlc_matvec")
+        return y
+
+    def matvec_noalloc(self, x, y):
+        """y = C~ x into the caller's device tensor y (x, y on the device)."""
+        _check(hlc_matvec_noalloc(self.ctx.h, self.h, _ptr(x), _ptr(y)), "hlc_matvec_noalloc")
         return y
 
 
