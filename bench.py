@@ -212,6 +212,8 @@ def serve_stream(hlc, inputs, dev, n_lo, n_hi, n_req, slots, seed=5000):
     ctx = hlc.Context(dev)
     ctx.serve_start(96 << 30, slots)
 
+    errors = []
+
     def drain(ids, t_limit=900.0):
         done, failed = {}, 0
         t0 = time.perf_counter()
@@ -221,7 +223,8 @@ def serve_stream(hlc, inputs, dev, n_lo, n_hi, n_req, slots, seed=5000):
                     continue
                 try:
                     r = ctx.serve_poll(i)
-                except hlc.HlcError:
+                except hlc.HlcError as e:
+                    errors.append(hlc.ERRORS.get(e.status, e.status))
                     failed += 1
                     ids[ids.index(i)] = -1
                     continue
@@ -255,7 +258,7 @@ def serve_stream(hlc, inputs, dev, n_lo, n_hi, n_req, slots, seed=5000):
         return lat[min(len(lat) - 1, int(math.ceil(p / 100.0 * len(lat))) - 1)]
 
     return {"p50_ms": pct(50), "p99_ms": pct(99), "evals_per_s": len(lat) / span, "requests": n_req,
-            "completed": len(lat), "failed": failed, "n_range": [n_lo, n_hi], "slots": slots,
+            "completed": len(lat), "failed": failed, "errors": errors, "n_range": [n_lo, n_hi], "slots": slots,
             "arrival_rate_per_s": rate, "closed_loop_capacity_per_s": capacity,
             "note": "Poisson arrivals at 0.8 x closed-loop capacity; mixed precision, eps 1e-6, leaf 64"}
 
