@@ -293,6 +293,8 @@ struct TermP {
   double alpha;
 };
 const int64_t kTruncBigRows = 4096;   // m + n above which a truncation uses a cluster
+const int64_t kTruncManyCols = 128;   // term columns (at capacity) beyond which ...
+const int64_t kTruncManyRows = 512;   // ... a target with m + n above this uses a cluster too
 const int64_t kGemmSplitRows = 4096;  // row block of a split product
 const int64_t kGemmSplitK = 2048;     // inner block of a split matrix-vector product
 const int64_t kPendingCols = INT64_MAX;  // no size-forced truncation: flush only on use
@@ -616,7 +618,12 @@ struct Planner {
     const int32_t w = place(reads, {U, V});
     P.trunc.push_back(op);
     // large targets run on a thread-block cluster
-    const int32_t ty = (B.m + B.n > kTruncBigRows) ? OP_TRUNC_BIG : OP_TRUNC;
+    // a cluster of CTAs streams the rows of large targets, and of mid-size
+    // targets that take many terms (several sequential batches of columns)
+    int64_t tcols = 0;
+    for (const TermP& t : terms) tcols += (t.flags & 1) ? t.urows : (t.flags & 2) ? t.vrows : t.k.n;
+    const bool many = tcols > kTruncManyCols && B.m + B.n > kTruncManyRows;
+    const int32_t ty = (B.m + B.n > kTruncBigRows || many) ? OP_TRUNC_BIG : OP_TRUNC;
     seq.push_back(Ref{ty, (int64_t)P.trunc.size() - 1, w});
   }
 

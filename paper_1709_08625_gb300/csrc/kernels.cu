@@ -252,35 +252,43 @@ __global__ void k_potrf(const OpPotrf* ops, int64_t count, Bases B) {
 }
 
 // ---------------------------------------------------------------------------
-// TRSM: X (n x c) := L^-1 X or L^-T X, L dense lower n x n (n <= 128).
-// One warp per column of X; lane i holds rows i, i+32, i+64, i+96.
+// TRSM: X (n x c) := L^-1 X or L^-T X, L dense lower n x n (n <= 128), in
+// arithmetic type T (FP32 in the mixed modes: the solves are panel operations
+// and preconditioner applications there; FP64 otherwise).
+// One warp per column of X; lane i holds rows i, i+32, i+64, i+96.  The
+// reciprocals of the diagonal are formed once, in parallel, so that the
+// sequential substitution chain multiplies instead of dividing.
+// sL: n * n + n entries of T.
 // ---------------------------------------------------------------------------
-__device__ void do_trsm(const OpTrsm& op, const Bases& B, double* sL) {
+template <class T>
+__device__ void do_trsm(const OpTrsm& op, const Bases& B, T* sL) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int n = op.n;
   const int c = dimv(op.c, B.ranks);
   if (B.flops && threadIdx.x == 0) atomicAdd(B.flops + OP_TRSM, (double)n * n * c);
   const double* L = vptr(B, op.L);
+  T* sInv = sL + n * n;
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     const int i = e % n, j = e / n;
-    sL[e] = L[i * op.L.rs + j * op.L.cs];
+    sL[e] = (T)L[i * op.L.rs + j * op.L.cs];
   }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) sInv[i] = T(1) / (T)L[i * op.L.rs + i * op.L.cs];
   __syncthreads();
   double* X = vptr(B, op.X);
   for (int col = w; col < c; col += nw) {
     double* xc = X + col * op.X.cs;
-    double x[4];
+    T x[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int r = lane + 32 * q;
-      x[q] = r < n ? xc[r * op.X.rs] : 0.0;
+      x[q] = r < n ? (T)xc[r * op.X.rs] : T(0);
     }
     if (!op.trans) {
       for (int i = 0; i < n; ++i) {
         const int owner = i & 31, qi = i >> 5;
-        double mine = qi == 0 ? x[0] : qi == 1 ? x[1] : qi == 2 ? x[2] : x[3];
-        if (lane == owner) mine /= sL[i + i * n];
-        const double xi = __shfl_sync(0xffffffffu, mine, owner);
+        T mine = qi == 0 ? x[0] : qi == 1 ? x[1] : qi == 2 ? x[2] : x[3];
+        if (lane == owner) mine *= sInv[i];
+        const T xi = __shfl_sync(0xffffffffu, mine, owner);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int r = lane + 32 * q;
@@ -291,9 +299,9 @@ __device__ void do_trsm(const OpTrsm& op, const Bases& B, double* sL) {
     } else {
       for (int i = n - 1; i >= 0; --i) {
         const int owner = i & 31, qi = i >> 5;
-        double mine = qi == 0 ? x[0] : qi == 1 ? x[1] : qi == 2 ? x[2] : x[3];
-        if (lane == owner) mine /= sL[i + i * n];
-        const double xi = __shfl_sync(0xffffffffu, mine, owner);
+        T mine = qi == 0 ? x[0] : qi == 1 ? x[1] : qi == 2 ? x[2] : x[3];
+        if (lane == owner) mine *= sInv[i];
+        const T xi = __shfl_sync(0xffffffffu, mine, owner);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int r = lane + 32 * q;
@@ -305,15 +313,20 @@ __device__ void do_trsm(const OpTrsm& op, const Bases& B, double* sL) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int r = lane + 32 * q;
-      if (r < n) xc[r * op.X.rs] = x[q];
+      if (r < n) xc[r * op.X.rs] = (double)x[q];
     }
   }
   __syncthreads();
 }
 
+// dynamic shared memory of a TRSM (the block and its inverted diagonal)
+static size_t trsm_smem(int max_dense) { return ((size_t)max_dense * max_dense + max_dense) * sizeof(double); }
+
+template <class T>
 __global__ void k_trsm(const OpTrsm* ops, int64_t count, Bases B) {
-  extern __shared__ double sL[];
-  for (int64_t o = blockIdx.x; o < count; o += gridDim.x) do_trsm(ops[o], B, sL);
+  extern __shared__ double smd[];
+  T* sL = reinterpret_cast<T*>(smd);
+  for (int64_t o = blockIdx.x; o < count; o += gridDim.x) do_trsm<T>(ops[o], B, sL);
 }
 
 // ---------------------------------------------------------------------------
@@ -508,7 +521,10 @@ __global__ void __launch_bounds__(256) k_waves(const WaveRange* waves, int nwave
     const int64_t tot = wr.ntrsm + wr.ngemm;
     for (int64_t o = blockIdx.x; o < tot; o += gridDim.x) {
       if (o < wr.ntrsm) {
-        do_trsm(trsm[wr.trsm0 + o], B, sL);
+        if (B.mixed)
+          do_trsm<float>(trsm[wr.trsm0 + o], B, reinterpret_cast<float*>(sL));
+        else
+          do_trsm<double>(trsm[wr.trsm0 + o], B, sL);
       } else if (B.mixed) {
         do_gemm<float>(gemm[wr.gemm0 + (o - wr.ntrsm)], B, gf);
       } else {
@@ -522,7 +538,7 @@ __global__ void __launch_bounds__(256) k_waves(const WaveRange* waves, int nwave
 int waves_grid(int max_dense) {
   int per = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_waves, 256,
-                                                    (size_t)max_dense * max_dense * sizeof(double)) != cudaSuccess)
+                                                    trsm_smem(max_dense)) != cudaSuccess)
     return 0;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -536,7 +552,7 @@ int launch_waves(const WaveRange* waves, int nwaves, const OpTrsm* trsm, const O
   if (grid <= 0 || nwaves <= 0 || !gb) return -1;
   if (cudaMemsetAsync(gb, 0, sizeof(GridBar), st) != cudaSuccess) return -1;
   void* args[] = {(void*)&waves, (void*)&nwaves, (void*)&trsm, (void*)&gemm, (void*)&B, (void*)&gb};
-  return cudaLaunchCooperativeKernel((void*)k_waves, grid, 256, args, (size_t)max_dense * max_dense * sizeof(double),
+  return cudaLaunchCooperativeKernel((void*)k_waves, grid, 256, args, trsm_smem(max_dense),
                                      st) == cudaSuccess
              ? 0
              : -1;
@@ -628,8 +644,10 @@ void launch_ops(int type, const void* ops, int64_t count, const TermD* terms, co
           (const OpPotrf*)ops, count, B);
       break;
     case OP_TRSM:
-      k_trsm<<<grid_for(count, 152 * 8), 256, (size_t)max_dense * max_dense * sizeof(double), st>>>(
-          (const OpTrsm*)ops, count, B);
+      if (B.mixed)
+        k_trsm<float><<<grid_for(count, 152 * 8), 256, trsm_smem(max_dense), st>>>((const OpTrsm*)ops, count, B);
+      else
+        k_trsm<double><<<grid_for(count, 152 * 8), 256, trsm_smem(max_dense), st>>>((const OpTrsm*)ops, count, B);
       break;
     case OP_GEMM:
       if (B.mixed)
@@ -674,8 +692,10 @@ void launch_logdet(const int64_t* offs, const int32_t* dims, int64_t count, cons
 int configure_kernels(int max_dense) {
   const size_t need = (size_t)max_dense * max_dense * sizeof(double);
   cudaError_t e1 = cudaFuncSetAttribute(k_potrf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
-  cudaError_t e2 = cudaFuncSetAttribute(k_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
-  cudaError_t e4 = cudaFuncSetAttribute(k_waves, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+  const int tneed = (int)trsm_smem(max_dense);
+  cudaError_t e2 = cudaFuncSetAttribute(k_trsm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, tneed);
+  if (e2 == cudaSuccess) e2 = cudaFuncSetAttribute(k_trsm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, tneed);
+  cudaError_t e4 = cudaFuncSetAttribute(k_waves, cudaFuncAttributeMaxDynamicSharedMemorySize, tneed);
   const int e3 = configure_trunc();
   return (e1 == cudaSuccess && e2 == cudaSuccess && e3 == 0 && e4 == cudaSuccess) ? 0 : -1;
 }

@@ -153,6 +153,102 @@ __device__ void qr_stream(F rowval, int nrows, int K, T* R, T* sC, double* sh) {
   }
 }
 
+// Tall-skinny QR for K <= 32 columns, warp-level: every warp streams its own
+// 32-row chunks, one row per lane held in registers, and folds them into its
+// own R (K x K, shared memory) by Householder steps on [R; chunk]; the
+// per-warp factors are then combined pairwise (R_a := qr([R_a; R_b])) in a
+// binary tree.  Within a step the pivot column is always v[0]: after the
+// step the row shifts left, so every register index is static.  The column
+// dot products of a step are summed by a reduce-scatter butterfly (31
+// shuffles; lane l ends with the sum for column l), and the resulting
+// updates reach every lane through a 32-entry shared array.
+constexpr int TSQR_LD = 32;
+
+template <class T>
+__device__ __forceinline__ void tsqr_absorb(T (&v)[32], int K, T* R, T* wsh) {
+  constexpr int RL = TSQR_LD;
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  for (int j = 0; j < K; ++j) {
+    const T x0 = v[0];
+    const T xn = warp_sum(x0 * x0);
+    const T alpha = R[j + j * RL];
+    T tau = T(0), sc = T(0), beta = alpha;
+    if (xn > T(0)) {
+      beta = -copysign(sqrt(alpha * alpha + xn), alpha);
+      tau = (beta - alpha) / beta;
+      sc = T(1) / (alpha - beta);
+    }
+    if (tau != T(0)) {
+      const T u0 = x0 * sc;  // the reflector's chunk part (its R part is 1 at row j)
+      const int nl = K - j;
+      T d[32];
+#pragma unroll
+      for (int l = 0; l < 32; ++l) d[l] = u0 * v[l];
+#pragma unroll
+      for (int h = 16; h > 0; h >>= 1) {
+        const bool hi = (lane & h) != 0;
+#pragma unroll
+        for (int t = 0; t < h; ++t) {
+          const T send = hi ? d[t] : d[t + h];
+          const T keep = hi ? d[t + h] : d[t];
+          d[t] = keep + __shfl_xor_sync(FULL, send, h);
+        }
+      }
+      T wv = T(0);
+      if (lane >= 1 && lane < nl) {
+        const T rjl = R[j + (j + lane) * RL];
+        wv = tau * (rjl + d[0]);
+        R[j + (j + lane) * RL] = rjl - wv;
+      }
+      if (lane == 0) R[j + j * RL] = beta;
+      wsh[lane] = wv;
+      __syncwarp();
+#pragma unroll
+      for (int l = 1; l < 32; ++l) v[l] -= wsh[l] * u0;
+    }
+#pragma unroll
+    for (int l = 0; l < 31; ++l) v[l] = v[l + 1];
+    v[31] = T(0);
+    __syncwarp();
+  }
+}
+
+// R (K x K upper, ld TR_KT) of the nrows x K matrix rowval(i, c), K <= 32;
+// sW: per warp a 32 x 32 factor, then per warp 32 entries and a flag.
+template <class T, class F>
+__device__ void qr_tsqr(F rowval, int nrows, int K, T* R, T* sW) {
+  constexpr int RL = TSQR_LD;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  T* Rw = sW + w * 32 * RL;
+  T* wsh = sW + nw * 32 * RL + w * 32;
+  for (int e = lane; e < 32 * RL; e += 32) Rw[e] = T(0);
+  __syncwarp();
+  T v[32];
+  for (int r0 = w * 32; r0 < nrows; r0 += nw * 32) {
+    const int row = r0 + lane;
+#pragma unroll
+    for (int l = 0; l < 32; ++l) v[l] = (l < K && row < nrows) ? (T)rowval(row, l) : T(0);
+    tsqr_absorb<T>(v, K, Rw, wsh);
+  }
+  __syncthreads();
+  // warp w holds rows iff w * 32 < nrows; a factor without rows is zero
+  for (int st = 1; st < nw; st <<= 1) {
+    if ((w % (2 * st)) == 0 && w + st < nw && (w + st) * 32 < nrows) {
+      const T* Rb = sW + (w + st) * 32 * RL;
+#pragma unroll
+      for (int l = 0; l < 32; ++l) v[l] = (l < K && lane < K && lane <= l) ? Rb[lane + l * RL] : T(0);
+      tsqr_absorb<T>(v, K, Rw, wsh);
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+    const int i = e % K, j = e / K;
+    R[i + (int64_t)j * TR_KT] = sW[i + j * RL];
+  }
+  __syncthreads();
+}
+
 template <class T>
 struct CoreShared {
   T cn[TR_KT];
@@ -606,7 +702,7 @@ __device__ int tr_batch(const OpTrunc& op, const TermD* tl, const int* ranks, in
 }
 
 template <class T, class C>
-__global__ void __launch_bounds__(TR_THREADS) k_trunc(const OpTrunc* ops, int64_t count, const TermD* terms,
+__global__ void __launch_bounds__(TR_THREADS, sizeof(T) == 4 ? 2 : 1) k_trunc(const OpTrunc* ops, int64_t count, const TermD* terms,
                                                        Bases B) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sC = reinterpret_cast<T*>(smraw);
@@ -647,9 +743,15 @@ __global__ void __launch_bounds__(TR_THREADS) k_trunc(const OpTrunc* ops, int64_
         atomicAdd(B.phase + 11, 1ull);
         atomicAdd(B.phase + 12, (unsigned long long)K);
       }
-      qr_stream<T>([&](int r, int c) { return cat_value(B, op, cat, 0, r, c); }, op.m, K, Pu, sC, sh);
-      phase_mark(B.phase, 1, tp);
-      qr_stream<T>([&](int r, int c) { return cat_value(B, op, cat, 1, r, c); }, op.n, K, Pv, sC, sh);
+      if (K <= 32) {
+        qr_tsqr<T>([&](int r, int c) { return cat_value(B, op, cat, 0, r, c); }, op.m, K, Pu, sC);
+        phase_mark(B.phase, 1, tp);
+        qr_tsqr<T>([&](int r, int c) { return cat_value(B, op, cat, 1, r, c); }, op.n, K, Pv, sC);
+      } else {
+        qr_stream<T>([&](int r, int c) { return cat_value(B, op, cat, 0, r, c); }, op.m, K, Pu, sC, sh);
+        phase_mark(B.phase, 1, tp);
+        qr_stream<T>([&](int r, int c) { return cat_value(B, op, cat, 1, r, c); }, op.n, K, Pv, sC, sh);
+      }
       phase_mark(B.phase, 2, tp);
       tr_core<T, C>(Pu, Pv, K, op.eps, op.kcap, M, W, J, X, Cu, Cv, cs, B.status, B.phase);
       tp = clock64();
@@ -670,7 +772,7 @@ __global__ void __launch_bounds__(TR_THREADS) k_trunc(const OpTrunc* ops, int64_
 
 // Cluster variant for large targets: the TR_CL CTAs of a cluster share one op.
 template <class T, class C>
-__global__ void __cluster_dims__(TR_CL, 1, 1) __launch_bounds__(TR_THREADS)
+__global__ void __cluster_dims__(TR_CL, 1, 1) __launch_bounds__(TR_THREADS, sizeof(T) == 4 ? 2 : 1)
     k_trunc_cl(const OpTrunc* ops, int64_t count, const TermD* terms, Bases B) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sC = reinterpret_cast<T*>(smraw);
@@ -715,21 +817,28 @@ __global__ void __cluster_dims__(TR_CL, 1, 1) __launch_bounds__(TR_THREADS)
       const int mu0 = (int)((int64_t)op.m * rk / TR_CL), mu1 = (int)((int64_t)op.m * (rk + 1) / TR_CL);
       const int nv0 = (int)((int64_t)op.n * rk / TR_CL), nv1 = (int)((int64_t)op.n * (rk + 1) / TR_CL);
       // 1. partial R factors of this CTA's rows
-      qr_stream<T>([&](int r, int c) { return cat_value(B, op, cat, 0, mu0 + r, c); }, mu1 - mu0, K, Pu, sC, sh);
-      qr_stream<T>([&](int r, int c) { return cat_value(B, op, cat, 1, nv0 + r, c); }, nv1 - nv0, K, Pv, sC, sh);
+      if (K <= 32) {
+        qr_tsqr<T>([&](int r, int c) { return cat_value(B, op, cat, 0, mu0 + r, c); }, mu1 - mu0, K, Pu, sC);
+        qr_tsqr<T>([&](int r, int c) { return cat_value(B, op, cat, 1, nv0 + r, c); }, nv1 - nv0, K, Pv, sC);
+      } else {
+        qr_stream<T>([&](int r, int c) { return cat_value(B, op, cat, 0, mu0 + r, c); }, mu1 - mu0, K, Pu, sC, sh);
+        qr_stream<T>([&](int r, int c) { return cat_value(B, op, cat, 1, nv0 + r, c); }, nv1 - nv0, K, Pv, sC, sh);
+      }
       __threadfence();
       cluster.sync();
       // 2. CTA 0 combines the U partials into its J region, CTA 1 the V partials
       if (rk < 2) {
         const int64_t poff = rk == 0 ? 0 : TR_REG;
         T* fin = reinterpret_cast<T*>(J);
-        qr_stream<T>(
-            [&](int r, int c) {
-              const T* P = reinterpret_cast<const T*>(scr_of(r / K) + poff);
-              const int i = r % K;
-              return i <= c ? (double)P[i + (int64_t)c * TR_KT] : 0.0;
-            },
-            TR_CL * K, K, fin, sC, sh);
+        auto part = [&](int r, int c) {
+          const T* P = reinterpret_cast<const T*>(scr_of(r / K) + poff);
+          const int i = r % K;
+          return i <= c ? (double)P[i + (int64_t)c * TR_KT] : 0.0;
+        };
+        if (K <= 32)
+          qr_tsqr<T>(part, TR_CL * K, K, fin, sC);
+        else
+          qr_stream<T>(part, TR_CL * K, K, fin, sC, sh);
       }
       __threadfence();
       cluster.sync();
@@ -767,14 +876,19 @@ __global__ void __cluster_dims__(TR_CL, 1, 1) __launch_bounds__(TR_THREADS)
   }
 }
 
-static size_t smem_bytes(bool f32) {
-  return f32 ? (size_t)TrCh<float>::value * TR_KT * sizeof(float) : (size_t)TrCh<double>::value * TR_KT * sizeof(double);
+// dynamic shared memory: the streamed chunk, or the per-warp R factors and
+// update arrays of the warp-level QR, whichever is larger
+template <class T, class C>
+static size_t smem_bytes() {
+  const size_t chunk = (size_t)TrCh<T>::elems * sizeof(T);
+  const size_t tsqr = (size_t)(TR_THREADS / 32) * 32 * (TSQR_LD + 1) * sizeof(T);
+  return chunk > tsqr ? chunk : tsqr;
 }
 
 template <class T, class C>
 static int configure_pair() {
   int bad = 0;
-  const int sm = (int)smem_bytes(sizeof(T) == 4);
+  const int sm = (int)smem_bytes<T, C>();
   bad |= cudaFuncSetAttribute(k_trunc<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess;
   bad |= cudaFuncSetAttribute(k_trunc_cl<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess;
   return bad;
@@ -789,7 +903,7 @@ template <class T, class C>
 static void launch_pair(const OpTrunc* ops, int64_t count, const TermD* terms, const Bases& B, bool big,
                         cudaStream_t st) {
   const int cap = max_trunc_ctas();
-  const size_t sm = smem_bytes(sizeof(T) == 4);
+  const size_t sm = smem_bytes<T, C>();
   if (!big) {
     const int grid = (int)(count < cap ? count : cap);
     k_trunc<T, C><<<grid, TR_THREADS, sm, st>>>(ops, count, terms, B);
