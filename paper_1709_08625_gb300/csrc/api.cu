@@ -42,6 +42,14 @@ struct hlc_ctx {
   double launches = 0;
   double op_launches[NOPTYPES] = {};
   double persistent_launches = 0;
+  // timed runs of the persistent kernel still to be read (grid tuning)
+  struct TuneRec {
+    const Plan* P;
+    int cand;
+    cudaEvent_t e0, e1;
+  };
+  std::vector<TuneRec> tune_pending;
+  std::vector<cudaEvent_t> tune_free;
   double op_ms[NOPTYPES] = {};
   std::vector<cudaEvent_t> evpool;
   struct Pending {
@@ -217,6 +225,10 @@ void run_plan_launches(hlc_tree* t, const Plan& P, const Bases& B, cudaStream_t 
 // Run a plan: replayed from a CUDA graph when possible (the op program is the
 // same for every evaluation on a tree; only the ranks in device memory vary),
 // captured on first use for a given set of base pointers.
+// CTAs per SM tried by the grid tuning of the persistent kernel (capped at
+// what fits on an SM when launched)
+constexpr int kTuneCandidates[3] = {1, 2, 4};
+
 bool persistent_enabled() {
   static const bool on = !(getenv("HLC_PERSISTENT") && getenv("HLC_PERSISTENT")[0] == '0');
   return on;
@@ -227,11 +239,44 @@ void run_plan(hlc_tree* t, const Plan& P, const Bases& B, cudaStream_t st) {
   // TRSM/GEMM plans (solves, matvec): one persistent cooperative launch
   if (P.d_waves && !P.waves.empty() && c->persistent && !c->profiling && !g_prof.on && persistent_enabled()) {
     const int md = (int)std::max<int64_t>(t->T.max_dense_dim, t->T.leaf);
-    if (launch_waves(P.d_waves, (int)P.waves.size(), P.d_trsm, P.d_gemm, B, c->d_gridbar, md, st) == 0) {
+    // autotuning of the grid: until the plan is tuned, every run takes the
+    // candidate with the fewest runs so far and is timed with events; the
+    // grid does not change the result (each op of a wave writes its own
+    // region), only the time
+    int per = P.tuned_per_sm, cand = -1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (per == 0) {
+      cand = 0;
+      for (int i = 1; i < 3; ++i)
+        if (P.tune_tries[i] < P.tune_tries[cand]) cand = i;
+      per = kTuneCandidates[cand];
+      for (cudaEvent_t* e : {&e0, &e1}) {
+        if (!c->tune_free.empty()) {
+          *e = c->tune_free.back();
+          c->tune_free.pop_back();
+        } else if (cudaEventCreate(e) != cudaSuccess) {
+          *e = nullptr;
+        }
+      }
+      if (e0 && e1) cudaEventRecord(e0, st);
+    }
+    if (launch_waves(P.d_waves, (int)P.waves.size(), P.d_trsm, P.d_gemm, B, c->d_gridbar, md, per, st) == 0) {
       c->launches += 1;
       c->persistent_launches += 1;
+      if (cand >= 0) {
+        P.tune_tries[cand] += 1;
+        if (e0 && e1) {
+          cudaEventRecord(e1, st);
+          c->tune_pending.push_back(hlc_ctx::TuneRec{&P, cand, e0, e1});
+          e0 = e1 = nullptr;
+        }
+      }
+      for (cudaEvent_t e : {e0, e1})
+        if (e) c->tune_free.push_back(e);
       return;
     }
+    for (cudaEvent_t e : {e0, e1})
+      if (e) c->tune_free.push_back(e);
     cudaGetLastError();
   }
   if (c->profiling || g_prof.on || !graphs_enabled() || P.launches.empty()) {
@@ -323,12 +368,38 @@ Bases make_bases(hlc_tree* t, double* mat_L, double* mat_C, int* ranks, bool mix
   return B;
 }
 
+// Timed runs of the persistent kernel (the stream has been synchronised):
+// record each candidate's best time; once every candidate has two runs the
+// plan keeps the fastest.
+void read_tuning(hlc_ctx* c) {
+  for (const hlc_ctx::TuneRec& r : c->tune_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.e0, r.e1) == cudaSuccess) {
+      float& best = r.P->tune_ms[r.cand];
+      if (r.P->tune_done[r.cand] == 0 || ms < best) best = ms;
+      r.P->tune_done[r.cand] += 1;
+      bool all = true;
+      int arg = 0;
+      for (int i = 0; i < 3; ++i) {
+        all = all && r.P->tune_done[i] >= 2;
+        if (r.P->tune_done[i] > 0 && r.P->tune_ms[i] < r.P->tune_ms[arg]) arg = i;
+      }
+      if (all && r.P->tuned_per_sm == 0) r.P->tuned_per_sm = kTuneCandidates[arg];
+    }
+    c->tune_free.push_back(r.e0);
+    c->tune_free.push_back(r.e1);
+  }
+  c->tune_pending.clear();
+  cudaGetLastError();
+}
+
 // device status -> ABI status (also resets it)
 int take_status(hlc_ctx* c) {
   int h[2] = {0, 0};
   cudaError_t e = cudaMemcpyAsync(h, c->d_status, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_status(e);
+  read_tuning(c);
   cudaMemsetAsync(c->d_status, 0, 2 * sizeof(int), c->stream);
   switch (h[0]) {
     case DEV_OK: return HLC_OK;
@@ -647,6 +718,11 @@ void hlc_destroy(hlc_ctx* c) {
     cudaFree(c->d_phase);
   }
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
+  for (const hlc_ctx::TuneRec& r : c->tune_pending) {
+    cudaEventDestroy(r.e0);
+    cudaEventDestroy(r.e1);
+  }
+  for (cudaEvent_t e : c->tune_free) cudaEventDestroy(e);
   for (int i = 0; i < 4; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
   if (c->stream) cudaStreamDestroy(c->stream);
@@ -743,6 +819,7 @@ void hlc_tree_free(hlc_tree* t) {
     return;
   }
   cudaStreamSynchronize(t->ctx->stream);
+  read_tuning(t->ctx);  // no timing record may outlive the tree's plans
   hlc_hmat_free(t->wsC);
   hlc_hmat_free(t->wsL);
   cudaFree(t->d_perm);
@@ -1129,7 +1206,7 @@ int hlc_matvec_noalloc(hlc_ctx* c, const hlc_hmat* C, const double* x, double* y
   B.buf[BUF_TMP] = S + 3 * n;
   const int md = (int)std::max<int64_t>(t->T.max_dense_dim, t->T.leaf);
   if (launch_waves(t->mv.d_waves, (int)t->mv.waves.size(), t->mv.d_trsm, t->mv.d_gemm, B, c->d_gridbar, md,
-                   c->stream) != 0) {
+                   t->mv.tuned_per_sm, c->stream) != 0) {
     cudaGetLastError();
     return HLC_ERR_CUDA;
   }

@@ -185,6 +185,13 @@ struct Plan {
   // waves of a TRSM/GEMM-only plan, for the persistent kernel
   std::vector<WaveRange> waves;
   WaveRange* d_waves = nullptr;
+  // online tuning of the persistent kernel's CTAs per SM: candidate i is
+  // launched tune_tries[i] times and its best event time is tune_ms[i];
+  // tuned_per_sm is set once every candidate has two timed runs
+  mutable int tuned_per_sm = 0;
+  mutable int tune_tries[3] = {0, 0, 0};
+  mutable int tune_done[3] = {0, 0, 0};
+  mutable float tune_ms[3] = {0.f, 0.f, 0.f};
   // device copies
   OpGemm* d_gemm = nullptr;
   OpTrsm* d_trsm = nullptr;

@@ -535,20 +535,22 @@ __global__ void __launch_bounds__(256) k_waves(const WaveRange* waves, int nwave
   }
 }
 
-int waves_grid(int max_dense) {
+// CTAs of the persistent kernel that fit on one SM (all must be resident)
+int waves_max_per_sm(int max_dense) {
   int per = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_waves, 256,
-                                                    trsm_smem(max_dense)) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_waves, 256, trsm_smem(max_dense)) != cudaSuccess)
     return 0;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  return per * sms;
+  return per;
 }
 
 int launch_waves(const WaveRange* waves, int nwaves, const OpTrsm* trsm, const OpGemm* gemm, const Bases& B,
-                 GridBar* gb, int max_dense, cudaStream_t st) {
-  const int grid = waves_grid(max_dense);
+                 GridBar* gb, int max_dense, int per_sm, cudaStream_t st) {
+  const int maxper = waves_max_per_sm(max_dense);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int per = (per_sm <= 0 || per_sm > maxper) ? maxper : per_sm;
+  const int grid = per * sms;
   if (grid <= 0 || nwaves <= 0 || !gb) return -1;
   if (cudaMemsetAsync(gb, 0, sizeof(GridBar), st) != cudaSuccess) return -1;
   void* args[] = {(void*)&waves, (void*)&nwaves, (void*)&trsm, (void*)&gemm, (void*)&B, (void*)&gb};

@@ -19,10 +19,12 @@ void launch_aca(const LrAsm* d, int64_t count, double* arena, const double* px, 
                 const MaternDev& mp, double eps, int* ranks, cudaStream_t st);
 void launch_ops(int type, const void* ops, int64_t count, const TermD* terms, const Bases& B, int max_dense,
                 cudaStream_t st);
-// One cooperative launch executing all waves of a TRSM/GEMM plan; -1 when the
+// One cooperative launch executing all waves of a TRSM/GEMM plan with
+// per_sm CTAs per SM (0 or more than fit: as many as fit); -1 when the
 // cooperative launch is unavailable (the caller then launches wave by wave).
 int launch_waves(const WaveRange* waves, int nwaves, const OpTrsm* trsm, const OpGemm* gemm, const Bases& B,
-                 GridBar* gb, int max_dense, cudaStream_t st);
+                 GridBar* gb, int max_dense, int per_sm, cudaStream_t st);
+int waves_max_per_sm(int max_dense);
 void launch_gather(const double* src, const int32_t* perm, double* dst, int64_t n, cudaStream_t st);
 void launch_scatter(const double* src, const int32_t* perm, double* dst, int64_t n, cudaStream_t st);
 void launch_points(const double* xy, const int32_t* perm, double* px, double* py, int64_t n, cudaStream_t st);

@@ -249,6 +249,51 @@ __device__ void qr_tsqr(F rowval, int nrows, int K, T* R, T* sW) {
   __syncthreads();
 }
 
+// Both R factors of a batch at once, for K <= 32: the first half of the
+// warps runs the tall-skinny QR of U's rows, the second half V's, each with
+// its own binary tree; the block barriers between tree levels are shared.
+template <class T, class FU, class FV>
+__device__ void qr_tsqr_pair(FU rowu, int mrows, FV rowv, int nrows, int K, T* Ru, T* Rv, T* sW) {
+  constexpr int RL = TSQR_LD;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int half = nw >> 1, side = w >= half, wl = w - side * half;
+  const int rows = side ? nrows : mrows;
+  T* Rw = sW + w * 32 * RL;
+  T* wsh = sW + nw * 32 * RL + w * 32;
+  for (int e = lane; e < 32 * RL; e += 32) Rw[e] = T(0);
+  __syncwarp();
+  T v[32];
+  for (int r0 = wl * 32; r0 < rows; r0 += half * 32) {
+    const int row = r0 + lane;
+    if (side) {
+#pragma unroll
+      for (int l = 0; l < 32; ++l) v[l] = (l < K && row < rows) ? (T)rowv(row, l) : T(0);
+    } else {
+#pragma unroll
+      for (int l = 0; l < 32; ++l) v[l] = (l < K && row < rows) ? (T)rowu(row, l) : T(0);
+    }
+    tsqr_absorb<T>(v, K, Rw, wsh);
+  }
+  __syncthreads();
+  for (int st = 1; st < half; st <<= 1) {
+    if ((wl % (2 * st)) == 0 && wl + st < half && (wl + st) * 32 < rows) {
+      const T* Rb = sW + (w + st) * 32 * RL;
+#pragma unroll
+      for (int l = 0; l < 32; ++l) v[l] = (l < K && lane < K && lane <= l) ? Rb[lane + l * RL] : T(0);
+      tsqr_absorb<T>(v, K, Rw, wsh);
+    }
+    __syncthreads();
+  }
+  const T* R0 = sW;
+  const T* R1 = sW + half * 32 * RL;
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+    const int i = e % K, j = e / K;
+    Ru[i + (int64_t)j * TR_KT] = R0[i + j * RL];
+    Rv[i + (int64_t)j * TR_KT] = R1[i + j * RL];
+  }
+  __syncthreads();
+}
+
 template <class T>
 struct CoreShared {
   T cn[TR_KT];
@@ -744,9 +789,9 @@ __global__ void __launch_bounds__(TR_THREADS, sizeof(T) == 4 ? 2 : 1) k_trunc(co
         atomicAdd(B.phase + 12, (unsigned long long)K);
       }
       if (K <= 32) {
-        qr_tsqr<T>([&](int r, int c) { return cat_value(B, op, cat, 0, r, c); }, op.m, K, Pu, sC);
+        qr_tsqr_pair<T>([&](int r, int c) { return cat_value(B, op, cat, 0, r, c); }, op.m,
+                        [&](int r, int c) { return cat_value(B, op, cat, 1, r, c); }, op.n, K, Pu, Pv, sC);
         phase_mark(B.phase, 1, tp);
-        qr_tsqr<T>([&](int r, int c) { return cat_value(B, op, cat, 1, r, c); }, op.n, K, Pv, sC);
       } else {
         qr_stream<T>([&](int r, int c) { return cat_value(B, op, cat, 0, r, c); }, op.m, K, Pu, sC, sh);
         phase_mark(B.phase, 1, tp);
