@@ -169,6 +169,17 @@ int hlc_matvec_noalloc(hlc_ctx* ctx, const hlc_hmat* C, const double* x, double*
 /* Capacity in doubles of the fixed buffer of hlc_matvec_noalloc. */
 int64_t hlc_matvec_noalloc_capacity(void);
 
+/*
+ * Self-test of the bounded device waits (no counterpart in the paper).  The
+ * persistent solve kernel separates its waves by a grid barrier whose wait is
+ * limited to 2 s; past the limit every CTA leaves the kernel and the call
+ * returns HLC_ERR_TIMEOUT.  This call makes two CTAs wait at a barrier that
+ * expects one arrival more than there are CTAs, so that only the limit can
+ * end the wait: it returns HLC_ERR_TIMEOUT after about 2 s, and the context
+ * stays usable.  Synchronous.
+ */
+int hlc_selftest_barrier_timeout(hlc_ctx* ctx);
+
 /* Dense expansion of C~ (symmetric) or L~ (lower) into an n x n column-major
  * host array in caller order; for small n only (n <= 16384). */
 int hlc_hmat_expand(hlc_ctx* ctx, const hlc_hmat* M, double* out);

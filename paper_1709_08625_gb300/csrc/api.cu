@@ -1182,6 +1182,16 @@ extern "C" {
 
 int64_t hlc_matvec_noalloc_capacity(void) { return kNoAllocDoubles; }
 
+int hlc_selftest_barrier_timeout(hlc_ctx* c) {
+  if (!c) return HLC_ERR_ARG;
+  CK(cudaSetDevice(c->device));
+  if (launch_barrier_probe(c->d_gridbar, c->d_status, c->stream) != 0) {
+    cudaGetLastError();
+    return HLC_ERR_CUDA;
+  }
+  return take_status(c);
+}
+
 int hlc_matvec_noalloc(hlc_ctx* c, const hlc_hmat* C, const double* x, double* y) {
   if (!c || !C || !x || !y || C->which != 0 || C->t->ctx != c) return HLC_ERR_ARG;
   if (!C->valid) return HLC_ERR_STATE;

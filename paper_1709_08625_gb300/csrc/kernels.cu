@@ -473,7 +473,10 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-__device__ bool grid_barrier(GridBar* gb, int* status) {
+// `expected`: arrivals that release the barrier (the grid size; the
+// self-test asks for one more than the grid has, so only the time limit can
+// end the wait).
+__device__ bool grid_barrier(GridBar* gb, int* status, unsigned int expected) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -483,7 +486,7 @@ __device__ bool grid_barrier(GridBar* gb, int* status) {
     if (good) {
       const unsigned int g = *gen;
       __threadfence();
-      if (atomicAdd(&gb->count, 1u) == gridDim.x - 1) {
+      if (atomicAdd(&gb->count, 1u) == expected - 1) {
         atomicExch(&gb->count, 0u);
         __threadfence();
         atomicAdd(&gb->gen, 1u);
@@ -531,8 +534,21 @@ __global__ void __launch_bounds__(256) k_waves(const WaveRange* waves, int nwave
         do_gemm<double>(gemm[wr.gemm0 + (o - wr.ntrsm)], B, gd);
       }
     }
-    if (w + 1 < nwaves && !grid_barrier(gb, B.status)) return;
+    if (w + 1 < nwaves && !grid_barrier(gb, B.status, gridDim.x)) return;
   }
+}
+
+// Self-test of the bounded wait: every CTA arrives, one arrival more is
+// expected, so the barrier ends only by its time limit (DEV_TIMEOUT).
+__global__ void k_barrier_probe(GridBar* gb, int* status) {
+  grid_barrier(gb, status, gridDim.x + 1);
+}
+
+int launch_barrier_probe(GridBar* gb, int* status, cudaStream_t st) {
+  if (!gb || !status) return -1;
+  if (cudaMemsetAsync(gb, 0, sizeof(GridBar), st) != cudaSuccess) return -1;
+  k_barrier_probe<<<2, 32, 0, st>>>(gb, status);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 // CTAs of the persistent kernel that fit on one SM (all must be resident)

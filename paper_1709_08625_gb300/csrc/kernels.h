@@ -25,6 +25,9 @@ void launch_ops(int type, const void* ops, int64_t count, const TermD* terms, co
 int launch_waves(const WaveRange* waves, int nwaves, const OpTrsm* trsm, const OpGemm* gemm, const Bases& B,
                  GridBar* gb, int max_dense, int per_sm, cudaStream_t st);
 int waves_max_per_sm(int max_dense);
+// Two CTAs wait at a grid barrier that expects one arrival more than the
+// grid has; the wait ends by its time limit with DEV_TIMEOUT in *status.
+int launch_barrier_probe(GridBar* gb, int* status, cudaStream_t st);
 void launch_gather(const double* src, const int32_t* perm, double* dst, int64_t n, cudaStream_t st);
 void launch_scatter(const double* src, const int32_t* perm, double* dst, int64_t n, cudaStream_t st);
 void launch_points(const double* xy, const int32_t* perm, double* px, double* py, int64_t n, cudaStream_t st);

@@ -82,6 +82,7 @@ _SIGS = {
     "hlc_matvec": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "hlc_matvec_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "hlc_matvec_noalloc_capacity": (ctypes.c_int64, []),
+    "hlc_selftest_barrier_timeout": (ctypes.c_int, [_vp]),
     "hlc_hmat_expand": (ctypes.c_int, [_vp, _vp, _vp]),
     "hlc_hmat_ranks": (ctypes.c_int, [_vp, _vp, _vp]),
     "hlc_hmat_free": (None, [_vp]),

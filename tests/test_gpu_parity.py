@@ -307,3 +307,21 @@ def test_persistent_solves_match_wave_launches(hlc):
     # take the ops does not change a single bit
     for key in ("loglik", "logdet", "quad", "quad_factor", "refine_iters"):
         assert on[key] == off[key], key
+
+
+# --------------------------------------------------------------------------
+# failure detection: a bounded device wait that runs out
+# --------------------------------------------------------------------------
+def test_bounded_wait_times_out_and_context_survives(ctx, hlc):
+    import time
+
+    t0 = time.time()
+    st = hlc.hlc_selftest_barrier_timeout(ctx.h)
+    dt = time.time() - t0
+    assert st == hlc.HLC_ERR_TIMEOUT
+    assert 1.5 < dt < 60.0
+    # the context keeps working after the timeout
+    n = 3000
+    r = ctx.build_tree(inputs.points(n, 1700), leaf=64, eps=1e-6).loglik(hlc.theta(1.0, 0.05, 0.5, 1e-4),
+                                                                        inputs.normal(n, 1701))
+    assert math.isfinite(r["loglik"]) and r["rel_residual"] <= 1e-10
