@@ -31,6 +31,21 @@
  *     Sec. 3) is reported as HLC_ERR_NOT_SPD; no NaN is returned.
  *   - All device work of a context runs on the context's stream; calls on one
  *     context must not overlap from several host threads.
+ *
+ * Environment switches (read once per process; the defaults are the product
+ * path, the others serve measurement and comparison):
+ *   HLC_ACCUMULATE=1  defer the updates of a low-rank block and truncate them
+ *                     together before its next use (default: every update is
+ *                     truncated at once)
+ *   HLC_PERSISTENT=0  run triangular solves and matvecs wave by wave instead of
+ *                     as one cooperative launch
+ *   HLC_GRAPHS=0      launch the op waves directly instead of replaying CUDA
+ *                     graphs
+ *   HLC_HOST_TREE=1   build the cluster and block trees on the host
+ *   HLC_PROFILE=1     time every op launch (synchronising) and print a summary
+ *                     at exit
+ *   HLC_PHASES=1      count clock cycles per phase of the truncation kernel and
+ *                     print them when the context is destroyed
  */
 #ifndef HLC_H
 #define HLC_H
