@@ -50,6 +50,11 @@ struct hlc_ctx {
   };
   std::vector<TuneRec> tune_pending;
   std::vector<cudaEvent_t> tune_free;
+  // side streams for the independent launches of one wave (POTRF, TRSM,
+  // GEMM), forked from and joined back into the context's stream
+  cudaStream_t side[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev_fork = nullptr, ev_join[3] = {nullptr, nullptr, nullptr};
+  bool side_ok = false;
   double op_ms[NOPTYPES] = {};
   std::vector<cudaEvent_t> evpool;
   struct Pending {
@@ -221,10 +226,8 @@ bool graphs_enabled() {
 }
 
 void run_plan_launches(hlc_tree* t, const Plan& P, const Bases& B, cudaStream_t st, bool count);
+void run_launch(hlc_tree* t, const Plan& P, const Bases& B, const Launch& L, int md, cudaStream_t st, bool count);
 
-// Run a plan: replayed from a CUDA graph when possible (the op program is the
-// same for every evaluation on a tree; only the ranks in device memory vary),
-// captured on first use for a given set of base pointers.
 // CTAs per SM tried by the grid tuning of the persistent kernel (capped at
 // what fits on an SM when launched)
 constexpr int kTuneCandidates[3] = {1, 2, 4};
@@ -234,6 +237,9 @@ bool persistent_enabled() {
   return on;
 }
 
+// Run a plan: replayed from a CUDA graph when possible (the op program is the
+// same for every evaluation on a tree; only the ranks in device memory vary),
+// captured on first use for a given set of base pointers.
 void run_plan(hlc_tree* t, const Plan& P, const Bases& B, cudaStream_t st) {
   hlc_ctx* c = t->ctx;
   // TRSM/GEMM plans (solves, matvec): one persistent cooperative launch
@@ -308,9 +314,49 @@ void run_plan(hlc_tree* t, const Plan& P, const Bases& B, cudaStream_t st) {
   for (const Launch& L : P.launches) c->op_launches[L.type] += 1;
 }
 
+// The ops of one wave are independent (the planner puts an op in the first
+// wave after all of its producers and earlier readers), so the POTRF, TRSM
+// and GEMM launches of a wave run on side streams beside the truncations,
+// forked from the context's stream at the start of the wave and joined back
+// before the next one (in a captured graph: parallel branches).  The two
+// truncation kernels stay on the context's stream: they share the per-CTA
+// scratch.  Timed (profiling) runs keep one stream.
 void run_plan_launches(hlc_tree* t, const Plan& P, const Bases& B, cudaStream_t st, bool count) {
   const int md = (int)std::max<int64_t>(t->T.max_dense_dim, t->T.leaf);
-  for (const Launch& L : P.launches) {
+  hlc_ctx* cx = t->ctx;
+  const bool conc = cx->side_ok && !cx->profiling && !g_prof.on;
+  size_t wave_end = 0;
+  bool forked = false, used[3] = {false, false, false};
+  for (size_t li = 0; li < P.launches.size(); ++li) {
+    const Launch& L = P.launches[li];
+    if (li == wave_end) {  // a new wave starts: its launches are [li, wave_end)
+      wave_end = li;
+      while (wave_end < P.launches.size() && P.launches[wave_end].wave == L.wave) ++wave_end;
+      forked = conc && wave_end - li > 1;
+      used[0] = used[1] = used[2] = false;
+      if (forked) cudaEventRecord(cx->ev_fork, st);
+    }
+    cudaStream_t ls = st;
+    if (forked && L.type <= OP_GEMM) {
+      ls = cx->side[L.type];
+      if (!used[L.type]) {
+        cudaStreamWaitEvent(ls, cx->ev_fork, 0);
+        used[L.type] = true;
+      }
+    }
+    run_launch(t, P, B, L, md, ls, count);
+    if (forked && li + 1 == wave_end) {
+      for (int k = 0; k < 3; ++k)
+        if (used[k]) {
+          cudaEventRecord(cx->ev_join[k], cx->side[k]);
+          cudaStreamWaitEvent(st, cx->ev_join[k], 0);
+        }
+    }
+  }
+}
+
+void run_launch(hlc_tree* t, const Plan& P, const Bases& B, const Launch& L, int md, cudaStream_t st, bool count) {
+  {
     const void* ops = nullptr;
     switch (L.type) {
       case OP_GEMM: ops = P.d_gemm + L.first; break;
@@ -334,11 +380,11 @@ void run_plan_launches(hlc_tree* t, const Plan& P, const Bases& B, cudaStream_t 
       launch_ops(L.type, ops, L.count, P.d_terms, B, md, st);
       cudaEventRecord(c->evpool[ev + 1], st);
       c->pending.push_back(hlc_ctx::Pending{L.type, ev});
-      continue;
+      return;
     }
     if (!g_prof.on) {
       launch_ops(L.type, ops, L.count, P.d_terms, B, md, st);
-      continue;
+      return;
     }
     cudaStreamSynchronize(st);
     const auto t0 = std::chrono::steady_clock::now();
@@ -657,6 +703,16 @@ int hlc_create(hlc_ctx** out, int device) {
   if (!c) return HLC_ERR_OOM;
   c->device = device;
   cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+  {
+    bool ok = e == cudaSuccess;
+    for (int k = 0; k < 3 && ok; ++k) {
+      ok = cudaStreamCreateWithFlags(&c->side[k], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&c->ev_join[k], cudaEventDisableTiming) == cudaSuccess;
+    }
+    ok = ok && cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    c->side_ok = ok;  // without side streams every launch stays on the context's stream
+    cudaGetLastError();
+  }
   if (e == cudaSuccess) e = cudaMalloc(&c->d_part, 1 << 20);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_scalar, 64);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_status, 16);
@@ -726,6 +782,11 @@ void hlc_destroy(hlc_ctx* c) {
   for (int i = 0; i < 4; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
   if (c->stream) cudaStreamDestroy(c->stream);
+  for (int k = 0; k < 3; ++k) {
+    if (c->side[k]) cudaStreamDestroy(c->side[k]);
+    if (c->ev_join[k]) cudaEventDestroy(c->ev_join[k]);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   delete c;
 }
 
