@@ -1,16 +1,19 @@
-// kernels.cu -- sm_103a kernels of the H-matrix likelihood (FP64 path).
+// kernels.cu -- sm_103a kernels of the H-matrix likelihood.
 //
 //   k_dense_asm   dense inadmissible leaves of C~ (eq. 3 + nugget, Sec. 4.1)
 //   k_aca         ACA with partial pivoting for admissible leaves (App. B)
-//   k_potrf       Cholesky of dense diagonal leaves (eq. 2)
-//   k_trsm        triangular solves with dense diagonal leaves
-//   k_gemm        strided multiply-add of dense views (H-arithmetic, Table 1)
-//   k_trunc       truncated low-rank sums: QR of both factors, SVD of the
-//                 core, keep sigma_i > eps sigma_1 (Remark A.1)
+//   k_potrf       Cholesky of dense diagonal leaves (eq. 2), FP64
+//   k_trsm        triangular solves with dense diagonal leaves (FP64, or
+//                 FP32 in the mixed modes)
+//   k_gemm        strided multiply-add of dense views (H-arithmetic, Table 1),
+//                 with a matrix-vector path for one column
+//   k_waves       a whole triangular solve or matvec as one cooperative launch
+//                 (waves separated by a bounded grid barrier)
 //   reductions    log det = 2 sum log L_ii, dot products (fixed order)
 //
-// Op kernels take a list of descriptors produced by the planner and loop
-// over it grid-stride, one op per CTA at a time.
+// The truncated low-rank sums (Remark A.1) are in trunc.cu.  Op kernels take
+// a list of descriptors produced by the planner and loop over it
+// grid-stride, one op per CTA at a time.
 
 #include <cuda_runtime.h>
 #include <math.h>

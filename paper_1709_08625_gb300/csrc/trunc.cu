@@ -8,11 +8,14 @@
 // factors Ucat (m x K), Vcat (n x K):
 //
 //   1. R_u, R_v: R factors of Ucat and Vcat by Householder QR streamed over
-//      row chunks ([R; chunk] -> R); Q is never formed;
+//      row chunks ([R; chunk] -> R); Q is never formed.  For K <= 32 a
+//      warp-level tall-skinny QR (both sides at once, qr_tsqr_pair), else
+//      block-wide (qr_stream);
 //   2. M = R_u R_v^T (K x K);
-//   3. the SVD of M: QR with column pivoting reduces M to its
-//      numerical rank r (the trailing part dropped is below 1e-3 eps |M|),
-//      then one-sided Jacobi on the r columns of (R P^T)^T: M = X S Y^T;
+//   3. the SVD of M: QR with column pivoting reduces M to its numerical rank
+//      r (the trailing part dropped is below max(1e-3 eps, 8 u) |M|), then
+//      one-sided Jacobi on the transpose of the R factor of (R P^T)^T:
+//      M = X S Y^T;
 //   4. keep the k values sigma_i > eps sigma_1 and write
 //        U_new = Ucat R_v^T Y_k S_k^-1/2 = Q_u X_k S_k^1/2,
 //        V_new = Vcat R_u^T X_k G^-1 S_k^-1/2,  G = X_k^T X_k (~ I),
@@ -25,9 +28,11 @@
 // whose R factors carry FP32 rounding already, FP64 in HLC_FP64 and
 // HLC_MIXED_SVD64; the core's stopping rules scale with its unit roundoff.
 //
-// Targets with m + n above 4096 rows run on a cluster of TR_CL CTAs: each CTA streams its share of the rows, CTAs 0 and 1 combine the
-// partial R factors, CTA 0 computes the core, all CTAs apply; the phases are
-// separated by cluster barriers.
+// Large targets (m + n above 4096 rows, or above 512 rows with many term
+// columns; the planner decides) run on a cluster of TR_CL CTAs: each CTA
+// streams its share of the rows, CTAs 0 and 1 combine the partial R factors,
+// CTA 0 computes the core, all CTAs apply; the phases are separated by
+// cluster barriers.
 
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
