@@ -382,3 +382,52 @@ def test_paper_table5_storage_order_of_magnitude():
     Hh.assemble(1.0, g["ell"], g["nu"], 1e-4, g["eps"])
     kb = Hh.stats()["entries_C"] * 8 / n / 1000.0
     assert row["kb_per_dof"] / 4 <= kb <= row["kb_per_dof"] * 2, kb
+
+
+def test_paper_table5_inverse_error_order_of_magnitude():
+    # Table 5 prints ||I - (L~ L~^T)^-1 C~||_2 = 2.4e-3 at n = 32,000 for
+    # nu=0.33, ell=0.65, sigma2=1, block accuracy 1e-5 for C~ and L~ (growing
+    # slowly with n).  The oracle at n = 2000 (nugget 1e-4) lands within a
+    # factor 10 of it.  The expansions are in caller order, where L~ is a
+    # permuted triangle, so the inverse goes through a Cholesky of L~ L~^T.
+    import scipy.linalg as sl
+
+    with open(os.path.join(GOLDEN, "table5_storage.json")) as f:
+        g = json.load(f)
+    target = g["rows"][0]["inv_err"]
+    n = 2000
+    xy = inputs.points(n, 95)
+    Hh = oracle.HOracle(xy, leaf=64)
+    Hh.assemble(1.0, g["ell"], g["nu"], 1e-4, g["eps"])
+    Hh.cholesky(g["eps"])
+    Ct, Lt = Hh.expand(0), Hh.expand(1)
+    cf = sl.cho_factor(Lt @ Lt.T)
+
+    def a(v):
+        return v - sl.cho_solve(cf, Ct @ v)
+
+    def at(v):
+        return v - Ct @ sl.cho_solve(cf, v)
+
+    v = np.random.default_rng(0).standard_normal(n)
+    v /= np.linalg.norm(v)
+    lam = 0.0
+    for _ in range(40):
+        y = at(a(v))
+        lam = np.linalg.norm(y)
+        v = y / lam
+    err = math.sqrt(lam)
+    assert target / 10 <= err <= target * 10, err
+
+
+def test_h_loglik_permutation_invariance():
+    # The tree depends on the point set, not on its order: permuting the
+    # locations (and z with them) gives the same likelihood.
+    n = 1500
+    xy = inputs.points(n, 96)
+    z = inputs.normal(n, 97)
+    p = np.random.default_rng(98).permutation(n)
+    r0 = oracle.h_loglik(xy, z, 1.0, 0.08, 0.5, 1e-4, 1e-7, leaf=32)
+    r1 = oracle.h_loglik(xy[p], z[p], 1.0, 0.08, 0.5, 1e-4, 1e-7, leaf=32)
+    assert abs(r1["loglik"] - r0["loglik"]) <= 1e-9 * abs(r0["loglik"])
+    assert abs(r1["logdet"] - r0["logdet"]) <= 1e-9 * abs(r0["logdet"])
