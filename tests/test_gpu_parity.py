@@ -325,3 +325,34 @@ def test_bounded_wait_times_out_and_context_survives(ctx, hlc):
     r = ctx.build_tree(inputs.points(n, 1700), leaf=64, eps=1e-6).loglik(hlc.theta(1.0, 0.05, 0.5, 1e-4),
                                                                         inputs.normal(n, 1701))
     assert math.isfinite(r["loglik"]) and r["rel_residual"] <= 1e-10
+
+
+# --------------------------------------------------------------------------
+# invariants of the likelihood on the GPU path
+# --------------------------------------------------------------------------
+def test_permutation_invariance(ctx, hlc):
+    # the tree depends on the point set, not its order: permuting the
+    # locations and z together gives the same evaluation, bit for bit
+    n = 6000
+    xy = inputs.points(n, 1800)
+    z = inputs.normal(n, 1801)
+    p = np.random.default_rng(1802).permutation(n)
+    th = hlc.theta(1.0, 0.05, 0.5, 1e-4)
+    r0 = ctx.build_tree(xy, leaf=64, eps=1e-6).loglik(th, z)
+    r1 = ctx.build_tree(xy[p], leaf=64, eps=1e-6).loglik(th, z[p])
+    assert r1["logdet"] == r0["logdet"]
+    assert abs(r1["loglik"] - r0["loglik"]) <= 1e-12 * abs(r0["loglik"])
+
+
+def test_variance_scaling_invariance(ctx, hlc):
+    # (sigma2, tau2) -> (a sigma2, a tau2): log det grows by n log a and the
+    # quadratic form shrinks by a (ACA pivots and truncation ranks are
+    # scale-free)
+    n, a = 5000, 2.5
+    xy = inputs.points(n, 1810)
+    z = inputs.normal(n, 1811)
+    t = ctx.build_tree(xy, leaf=64, eps=1e-7)
+    r0 = t.loglik(hlc.theta(1.0, 0.05, 1.5, 1e-4), z)
+    r1 = t.loglik(hlc.theta(a, 0.05, 1.5, a * 1e-4), z)
+    assert abs(r1["logdet"] - (r0["logdet"] + n * math.log(a))) <= 1e-9 * abs(r0["logdet"])
+    assert abs(r1["quad"] - r0["quad"] / a) <= 1e-9 * r0["quad"]
