@@ -336,13 +336,15 @@ def run_ours(args, rank, ws, local, dist):
     prof_ms = pe0.elapsed_time(pe1)
 
     # ---- end to end through the public API with host buffers ---------------
+    # (a step is ~50 s at the default workload: one step per rank suffices)
+    e2e_steps = min(args.steps, 1) if args.steps > 0 else 0
     t0 = time.perf_counter()
-    e2e_res = None
-    for k in range(args.steps):
+    e2e_res = results[-1] if results else None
+    for k in range(e2e_steps):
         e2e_res = tree.loglik(theta(1000 + k), z_pin.numpy())
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(dist, time.perf_counter() - t0)
-    e2e_value = ws * args.steps / e2e_s
+    e2e_value = ws * e2e_steps / e2e_s if e2e_steps else None
     info = tree.info()
     iters = e2e_res["refine_iters"]
     # bytes read back per evaluation: scalars of the solve, status words and
@@ -375,7 +377,8 @@ def run_ours(args, rank, ws, local, dist):
                        "l2": "no flush: H-matrix working set of several GB > 129 MB L2",
                        "parallelism": f"replicas x{ws}", "tree_build_s": tree_s, "warmup_s": warm_s,
                        "plan_ops": info["plan_ops"], "plan_waves": info["plan_waves"]},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps},
             "gpu_launches": int(cnt["launches"]),
             "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
                          "frac": achieved / peak if peak else None, "traffic": None,
