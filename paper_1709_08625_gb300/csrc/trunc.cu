@@ -302,6 +302,8 @@ __device__ void qr_tsqr_pair(FU rowu, int mrows, FV rowv, int nrows, int K, T* R
 template <class T>
 struct CoreShared {
   T cn[TR_KT];
+  T cn2[TR_KT];
+  T scl[TR_KT];
   T tauq[TR_KT];
   T sv[TR_KT];
   int piv[TR_KT];
@@ -341,42 +343,46 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, C
   // (or 8 unit roundoffs of the core type, when that is larger)
   const C stop_rel = (C)fmax(1e-3 * eps, sizeof(C) == 8 ? 8.0 * 2.220446049250313e-16 : 8.0 * 1.1920929e-7);
     int r = 0;
+  // Column norms once; afterwards every warp recomputes the norm (below the
+  // current row) of each column it updates, into the other of two buffers,
+  // so that the pivot choice of a step reads a buffer nobody writes.  Every
+  // warp picks the pivot itself (same data, same result), computes the
+  // reflector of the pivot column itself, and applies it with its scale
+  // folded in; the diagonal of R and the scaled reflectors are written after
+  // the loop.  Two block barriers per pivot.
+  C* cn0 = cs.cn;
+  C* cn1 = cs.cn2;
+  for (int j = w; j < K; j += nw) {
+    C p = C(0);
+    for (int i = lane; i < K; i += 32) p += M[i + (int64_t)j * TR_KT] * M[i + (int64_t)j * TR_KT];
+    p = warp_sum(p);
+    if (lane == 0) cn0[j] = p;
+  }
+  __syncthreads();
+  C ref = C(0);
   for (; r < K; ++r) {
-    for (int j = r + w; j < K; j += nw) {
-      C p = C(0);
-      for (int i = r + lane; i < K; i += 32) p += M[i + (int64_t)j * TR_KT] * M[i + (int64_t)j * TR_KT];
-      p = warp_sum(p);
-      if (lane == 0) cs.cn[j] = p;
-    }
-    __syncthreads();
-    if (w == 0) {
-      int jm = -1;
-      C best = C(-1), rem = C(0);
-      for (int j = r + lane; j < K; j += 32) {
-        rem += cs.cn[j];
-        if (cs.cn[j] > best) {
-          best = cs.cn[j];
-          jm = j;
-        }
-      }
-      rem = warp_sum(rem);
-      for (int o = 16; o > 0; o >>= 1) {  // max, ties to the smaller index
-        const C ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oj = __shfl_xor_sync(0xffffffffu, jm, o);
-        if (ob > best || (ob == best && oj >= 0 && (jm < 0 || oj < jm))) {
-          best = ob;
-          jm = oj;
-        }
-      }
-      if (lane == 0) {
-        cs.jmax = jm;
-        if (r == 0) cs.red[0] = sqrt(best);
-        cs.stop = (cs.red[0] == C(0)) || !(sqrt(rem) > stop_rel * cs.red[0]);
+    const C* cur = (r & 1) ? cn1 : cn0;
+    C* nxt = (r & 1) ? cn0 : cn1;
+    int jm = -1;
+    C best = C(-1), rem = C(0);
+    for (int j = r + lane; j < K; j += 32) {
+      rem += cur[j];
+      if (cur[j] > best) {
+        best = cur[j];
+        jm = j;
       }
     }
-    __syncthreads();
-    if (cs.stop) break;
-    const int jm = cs.jmax;
+    rem = warp_sum(rem);
+    for (int o = 16; o > 0; o >>= 1) {  // max, ties to the smaller index
+      const C ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oj = __shfl_xor_sync(0xffffffffu, jm, o);
+      if (ob > best || (ob == best && oj >= 0 && (jm < 0 || oj < jm))) {
+        best = ob;
+        jm = oj;
+      }
+    }
+    if (r == 0) ref = sqrt(best);
+    if (ref == C(0) || !(sqrt(rem) > stop_rel * ref)) break;
     if (jm != r) {
       for (int i = tid; i < K; i += blockDim.x) {
         const C a = M[i + (int64_t)r * TR_KT];
@@ -390,38 +396,49 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, C
       }
     }
     __syncthreads();
-    if (w == 0) {
-      C xn = C(0);
-      for (int i = r + 1 + lane; i < K; i += 32) xn += M[i + (int64_t)r * TR_KT] * M[i + (int64_t)r * TR_KT];
-      xn = warp_sum(xn);
-      const C alpha = M[r + (int64_t)r * TR_KT];
-      C tau = C(0), sc = C(0), beta = alpha;
-      if (xn > C(0)) {
-        beta = -copysign(sqrt(alpha * alpha + xn), alpha);
-        tau = (beta - alpha) / beta;
-        sc = C(1) / (alpha - beta);
-      }
-      if (tau != C(0))
-        for (int i = r + 1 + lane; i < K; i += 32) M[i + (int64_t)r * TR_KT] *= sc;
-      if (lane == 0) {
-        M[r + (int64_t)r * TR_KT] = beta;
-        cs.tauq[r] = tau;
-      }
+    C xn = C(0);
+    for (int i = r + 1 + lane; i < K; i += 32) xn += M[i + (int64_t)r * TR_KT] * M[i + (int64_t)r * TR_KT];
+    xn = warp_sum(xn);
+    const C alpha = M[r + (int64_t)r * TR_KT];
+    C tau = C(0), sc = C(1), beta = alpha;
+    if (xn > C(0)) {
+      beta = -copysign(sqrt(alpha * alpha + xn), alpha);
+      tau = (beta - alpha) / beta;
+      sc = C(1) / (alpha - beta);
     }
-    __syncthreads();
-    const C tau = cs.tauq[r];
-    if (tau != C(0)) {
-      for (int l = r + 1 + w; l < K; l += nw) {
-        C p = C(0);
-        for (int i = r + 1 + lane; i < K; i += 32) p += M[i + (int64_t)r * TR_KT] * M[i + (int64_t)l * TR_KT];
-        p = warp_sum(p);
-        const C wv = tau * (p + M[r + (int64_t)l * TR_KT]);
-        for (int i = r + 1 + lane; i < K; i += 32) M[i + (int64_t)l * TR_KT] -= wv * M[i + (int64_t)r * TR_KT];
-        if (lane == 0) M[r + (int64_t)l * TR_KT] -= wv;
+    if (tid == 0) {
+      cs.tauq[r] = tau;
+      cs.sv[r] = beta;  // the diagonal of R, written after the loop
+      cs.scl[r] = sc;
+    }
+    for (int l = r + 1 + w; l < K; l += nw) {
+      C p = C(0);
+      for (int i = r + 1 + lane; i < K; i += 32) p += M[i + (int64_t)r * TR_KT] * M[i + (int64_t)l * TR_KT];
+      p = warp_sum(p);
+      const C wv = tau * (M[r + (int64_t)l * TR_KT] + sc * p), ws = wv * sc;
+      C q = C(0);
+      for (int i = r + 1 + lane; i < K; i += 32) {
+        const C v = M[i + (int64_t)l * TR_KT] - ws * M[i + (int64_t)r * TR_KT];
+        M[i + (int64_t)l * TR_KT] = v;
+        q += v * v;
+      }
+      q = warp_sum(q);
+      if (lane == 0) {
+        M[r + (int64_t)l * TR_KT] -= wv;
+        nxt[l] = q;
       }
     }
     __syncthreads();
   }
+  // the diagonal of R and the reflectors scaled to a unit leading entry
+  for (int e = tid; e < r * K; e += blockDim.x) {
+    const int q = e / K, i = e % K;
+    if (i == q)
+      M[q + (int64_t)q * TR_KT] = cs.sv[q];
+    else if (i > q && cs.tauq[q] != C(0))
+      M[i + (int64_t)q * TR_KT] *= cs.scl[q];
+  }
+  __syncthreads();
   const int rank = r;
   (void)X;
   phase_mark(ph, 4, t0);
