@@ -328,7 +328,7 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, C
                         unsigned long long* ph = nullptr) {
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
   long long t0 = clock64();
-  // M = Ru Rv^C (both upper triangular)
+  // M = Ru Rv^T (both upper triangular)
   for (int e = tid; e < K * K; e += blockDim.x) {
     const int i = e % K, j = e / K;
     C s = C(0);
@@ -448,7 +448,7 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, C
     __syncthreads();
     return;
   }
-  // B = (R P^C)^C (K x rank) into W
+  // B = (R P^T)^T (K x rank) into W
   for (int e = tid; e < K * rank; e += blockDim.x) {
     const int j = e % K, i = e / K;  // R(i, j) -> B(piv[j], i)
     W[cs.piv[j] + (int64_t)i * TR_KT] = (i <= j) ? M[i + (int64_t)j * TR_KT] : C(0);
@@ -490,7 +490,7 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, C
     }
     __syncthreads();
   }
-  // The one-sided Jacobi works on A = R_B^C (lower triangular; the
+  // The one-sided Jacobi works on A = R_B^T (lower triangular; the
   // transpose of the triangular factor is what the QR preconditioning makes
   // nearly orthogonal), in the X region; J accumulates its rotations.
   C* A = X;
@@ -593,9 +593,9 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, C
   }
   __syncthreads();
   const int k = cs.k;
-  // The Jacobi gives R_B^C J = Wa (orthogonal columns, Wa = Wa_n S), so
-  // R_B = J S Wa_n^C, B = Q_B R_B = (Q_B J) S Wa_n^C, and with M = Q R P^C =
-  // Q B^C = (Q Wa_n) S (Q_B J)^C:
+  // The Jacobi gives R_B^T J = Wa (orthogonal columns, Wa = Wa_n S), so
+  // R_B = J S Wa_n^T, B = Q_B R_B = (Q_B J) S Wa_n^T, and with M = Q R P^T =
+  // Q B^T = (Q Wa_n) S (Q_B J)^T:
   //   left vectors of M:  x_c = Q [Wa_n(:, j_c); 0]  (reflectors of the pivoted QR, in M)
   //   right vectors of M: y_c = Q_B [J(:, j_c); 0]   (reflectors of the QR of B, in W)
   // Both are built in the Cu/Cv regions' columns (K x k each) before the
@@ -627,10 +627,10 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, C
     }
   }
   __syncthreads();
-  // G = X_k^C X_k, the Gram matrix of the kept left vectors (the identity up
+  // G = X_k^T X_k, the Gram matrix of the kept left vectors (the identity up
   // to the orthogonality the Jacobi reached), lower triangle in the X region
-  // (A is no longer needed).  V_new carries G^-1: then U_new V_new^C =
-  // Q_u P M Q_v^C with P the orthogonal projector onto span(X_k), whose
+  // (A is no longer needed).  V_new carries G^-1: then U_new V_new^T =
+  // Q_u P M Q_v^T with P the orthogonal projector onto span(X_k), whose
   // distance from M is bounded by the dropped columns whether or not X_k is
   // exactly orthogonal (in FP32 it is only to ~1e-6, which is not below eps).
   C* G = X;
@@ -644,7 +644,7 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, C
     G[i + (int64_t)j * TR_KT] = g;
   }
   __syncthreads();
-  // G = L L^C in place (warp 0, left-looking); G is near the identity, so a
+  // G = L L^T in place (warp 0, left-looking); G is near the identity, so a
   // pivot below 1/4 means the vectors are unusable and the correction is
   // skipped
   if (w == 0) {
@@ -667,7 +667,7 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, C
     }
     if (lane == 0) cs.rot = ok;
   }
-  // Cu = R_v^C y_c / s^0.5 and Cv = R_u^C x_c, one entry per thread; y_c,
+  // Cu = R_v^T y_c / s^0.5 and Cv = R_u^T x_c, one entry per thread; y_c,
   // x_c sit in Cu, Cv, the results go to W, M (free now)
   for (int e = tid; e < K * k; e += blockDim.x) {
     const int col = e % K, c = e / K;
@@ -683,7 +683,7 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, C
     M[col + (int64_t)c * TR_KT] = b;
   }
   __syncthreads();
-  // each row of R_u^C X_k times G^-1 (one thread per row), then S^-1/2
+  // each row of R_u^T X_k times G^-1 (one thread per row), then S^-1/2
   if (cs.rot) {
     for (int col = tid; col < K; col += blockDim.x) {
       C* row = M + col;
