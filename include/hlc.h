@@ -107,6 +107,14 @@ typedef struct {
   double quad_factor;  /* v^T v with L~ v = z (eq. 2 as printed) */
   int refine_iters;    /* preconditioned CG iterations */
   double rel_residual; /* |z - C~ x| / |z| at exit */
+  double est_rel_err;  /* estimate of |I - (L~ L~^T)^-1 C~|_2 (Table 5's last
+                          column): the largest distance from 1 of the Ritz
+                          values that the CG iterations give for the
+                          preconditioned operator (Lanczos); a lower bound
+                          that tightens with refine_iters; -1 without an
+                          iteration.  The factor's error against C~ in the
+                          2-norm; the refined quadratic form itself is exact
+                          to rel_residual times the condition of C~. */
   size_t bytes_C;      /* storage of C~ (actual ranks) */
   size_t bytes_L;      /* storage of L~ (actual ranks) */
   int max_rank_C, max_rank_L;
@@ -143,6 +151,14 @@ void hlc_tree_free(hlc_tree* t);
 /* info[8] = {n, clusters, leaf clusters, dense leaves, low-rank leaves,
  *            depth, plan ops, plan waves}. */
 int hlc_tree_info(const hlc_tree* t, int64_t* info);
+/* Device memory a tree holds, in bytes (host array of 6): out[0] one
+ * H-matrix arena (blocks at their rank capacity, and the rank words),
+ * out[1] H-matrices kept as the tree's evaluation workspace (0..2; both
+ * after the first hlc_loglik), out[2] plan temporaries, out[3] vectors and
+ * point / block descriptors, out[4] op programs, out[5] the total
+ * out[0] * out[1] + out[2] + out[3] + out[4].  Plans and workspaces appear
+ * once built (the first hlc_loglik on the tree builds all of them). */
+int hlc_tree_memory(const hlc_tree* t, int64_t* out);
 /* perm[i] = caller index of the point at tree position i (host array of n). */
 int hlc_tree_perm(const hlc_tree* t, int32_t* perm);
 /* Leaf blocks, 5 int64 each {row lo, row hi, col lo, col hi, type (0 dense,
@@ -163,9 +179,51 @@ int hlc_cholesky(hlc_ctx* ctx, const hlc_hmat* C, hlc_hmat** L);
 int hlc_matvec(hlc_ctx* ctx, const hlc_hmat* C, const double* x, double* y);
 
 /*
+ * Product with the H-Cholesky factor L~ (from hlc_cholesky): y = L~ x
+ * (trans = 0) or y = L~^T x (trans = 1), FP64 arithmetic.  In caller order
+ * this is P L~ P^T x with P the tree permutation, so that L~ L~^T is C~ in
+ * caller order.  x, y: n values, host or device.  Synchronous.
+ */
+int hlc_factor_apply(hlc_ctx* ctx, const hlc_hmat* L, int trans, const double* x, double* y);
+
+/*
+ * Synthetic data of Sec. 5.1: the H-Cholesky factorisation C~(theta) = L~ L~^T
+ * on the tree (in the tree's precision mode), then z = L~ xi in caller order,
+ * so that z ~ N(0, C~(theta)) when xi ~ N(0, I).  xi, z: n values, host or
+ * device; the caller draws xi.  Uses the tree's evaluation workspace (a later
+ * hlc_loglik on the tree overwrites it).  Synchronous.
+ */
+int hlc_sample(hlc_ctx* ctx, hlc_tree* t, const hlc_theta* th, const double* xi, double* z);
+
+/*
+ * Accuracy diagnostics of the H-approximation at theta (Sec. 3: Tables 2, 3
+ * and 5): assembles C~(theta) and its factor L~ on the tree (the tree's
+ * evaluation workspace), then estimates with `iters` power iterations from
+ * seeded random starts (FP64, tree order):
+ *   out[0] |C - C~|_2      (C the exact covariance, evaluated on the fly)
+ *   out[1] |C|_2
+ *   out[2] |C~ - L~ L~^T|_2
+ *   out[3] |I - (L~ L~^T)^-1 C~|_2 (Table 5's last column; power iteration
+ *          on A^T A)
+ *   out[4] KLD(C, C~) of Sec. 3 (zero means), to second order
+ *          1/4 |L~^-1 (C - C~) L~^-T|_F^2, estimated with `probes` Gaussian
+ *          probes (0: not estimated)
+ *   out[5] |C~|_2
+ * Power-iteration values approach the norms from below.  out[0], out[1] and
+ * out[4] need O(n^2) covariance evaluations per product and are computed for
+ * n <= 131072 only; -1 marks a value not computed.  Allocates a few vectors
+ * of n doubles for the call.  Synchronous.
+ */
+int hlc_diagnostics(hlc_ctx* ctx, hlc_tree* t, const hlc_theta* th, int iters, int probes, uint64_t seed,
+                    double* out);
+
+/*
  * y = C~ x without allocating device memory (the paper has no counterpart:
  * this is an interface for callers that may not allocate during a call).
- * Same result, bit for bit, as hlc_matvec on the same C~ and x.
+ * Same result, bit for bit, as hlc_matvec on the same C~ and x.  Like every
+ * plan run, it executes as one persistent launch unless the context is a
+ * serve slot or HLC_PERSISTENT=0 (or the cooperative launch is unavailable),
+ * and wave by wave otherwise.
  *   x, y      device pointers, n doubles each in caller order (host pointers
  *             -> HLC_ERR_ARG); borrowed for the call, synchronous.
  *   scratch   one fixed buffer of hlc_matvec_noalloc_capacity() doubles
@@ -214,6 +272,64 @@ void hlc_hmat_free(hlc_hmat* M);
 int hlc_loglik(hlc_ctx* ctx, hlc_tree* t, const hlc_theta* th, const double* z,
                hlc_result* out);
 
+/* ---- identification of theta (Sec. 5, App. B) ------------------------------ */
+/* Objective of hlc_nelder_mead: f(x, user) for x of the call's dimension;
+ * NaN counts as +inf. */
+typedef double (*hlc_objective)(const double* x, void* user);
+
+/*
+ * The simplex method of Nelder and Mead (Comput. J. 7, 1965, in the form of
+ * Lagarias et al., SIAM J. Optim. 9, 1998), the minimiser of the App. B
+ * listing; host code, no device work.  Coefficients: reflection 1, expansion
+ * 2, contraction 1/2, shrink 1/2.  Starts from the simplex x, x + step_i e_i
+ * and iterates until the simplex size (root mean square distance of the
+ * vertices from their centroid) is below size_tol or max_iter iterations
+ * have run.  x (dim values, 1 <= dim <= 64) is overwritten with the best
+ * vertex; *fmin, *iters (either may be NULL) get its value and the
+ * iterations run.
+ */
+int hlc_nelder_mead(int dim, double* x, const double* step, double size_tol, int max_iter, hlc_objective f,
+                    void* user, double* fmin, int* iters);
+
+typedef struct {
+  double step[3];   /* initial simplex steps for (nu, ell, sigma2) */
+  double size_tol;  /* stop below this simplex size */
+  int max_iter;     /* iteration limit */
+  int free_mask;    /* parameters identified: bit 0 nu, 1 ell, 2 sigma2 (7 = all
+                       three, as in the paper); the others stay at start */
+} hlc_fit_opts;
+
+/* The App. B settings: steps 0.02 (nu), 0.04 (ell), 0.01 (sigma2), size
+ * tolerance 1e-5, 200 iterations, all three parameters free. */
+void hlc_default_fit_opts(hlc_fit_opts* o);
+
+typedef struct {
+  hlc_theta theta;   /* identified parameters (nugget as given in start) */
+  double loglik;     /* L~ at theta */
+  int iterations;    /* simplex iterations */
+  int evaluations;   /* likelihood evaluations (each one hlc_loglik) */
+  int failed_evals;  /* evaluations outside the parameter domain or whose
+                        factorisation failed (counted as L = -inf) */
+  int converged;     /* 1: stopped by the size tolerance, 0: by max_iter */
+  int traced;        /* rows written to trace */
+  double ms_total;   /* wall time of the whole fit */
+} hlc_fit_result;
+
+/*
+ * Maximum-likelihood identification of theta = (nu, ell, sigma2) on one
+ * tree (Sec. 5; the App. B listing): Nelder-Mead on -L~(theta), each
+ * evaluation a full hlc_loglik (assembly, H-Cholesky, log det, solve) on the
+ * device with the tree's parameters.  z: n values in caller order, host or
+ * device.  start: the initial guess (its nugget stays fixed).  opts may be
+ * NULL for the App. B settings.  trace (optional, trace_cap rows of 5
+ * doubles): every evaluation as {nu, ell, sigma2, loglik, status}.
+ * A point outside the domain (a parameter <= 0, nu >= 20) or whose
+ * factorisation fails (HLC_ERR_NOT_SPD / NUMERIC / RANK) counts as
+ * L = -inf; any other error ends the fit and is returned.
+ */
+int hlc_fit(hlc_ctx* ctx, hlc_tree* t, const double* z, const hlc_theta* start, const hlc_fit_opts* opts,
+            double* trace, int trace_cap, hlc_fit_result* out);
+
 /* ---- measurement ---------------------------------------------------------- */
 /* The context's CUDA stream (cudaStream_t) in *stream, for timing with events
  * recorded on the stream the kernels run on. */
@@ -250,6 +366,23 @@ int hlc_serve_submit(hlc_ctx* ctx, const double* xy, const double* z, int64_t n,
 int hlc_serve_poll(hlc_ctx* ctx, uint64_t req_id, hlc_result* out);
 /* Finish every queued request, then stop the loop. */
 int hlc_serve_stop(hlc_ctx* ctx);
+
+/* The device footprint (bytes) the request loop charges against its budget
+ * for one request of n points with parameters p (NULL: defaults): two arenas
+ * of n (3 leaf + 7.5 log2(n/leaf) kmax) doubles each, temporaries and
+ * vectors.  0 for invalid arguments.  Host only. */
+size_t hlc_serve_footprint(int64_t n, const hlc_params* p);
+
+/* Host-only replay of the request loop's admission rule (no device work, no
+ * context): nreq requests queued at time 0 in index order, request i holding
+ * footprint[i] bytes for duration[i] time units once admitted, max_slots
+ * slots and a budget of `budget` bytes.  The rule is the one the slot
+ * workers apply: the head of the queue is admitted when a slot is free and
+ * its footprint fits in what is left of the budget, or when nothing runs.
+ * Outputs start[i] (admission time of request i) and *peak (largest sum of
+ * footprints running at once).  HLC_ERR_ARG for invalid arguments. */
+int hlc_serve_admission_replay(size_t budget, int max_slots, int64_t nreq, const size_t* footprint,
+                               const double* duration, double* start, size_t* peak);
 
 #ifdef __cplusplus
 }

@@ -71,6 +71,7 @@ def lib():
         L.orc_h_ranks.restype = ctypes.c_long
         L.orc_h_matvec.argtypes = [ctypes.c_void_p, _dp, _dp]
         L.orc_h_expand.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp]
+        L.orc_h_lmatvec.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, _dp]
         L.orc_h_loglik.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double, ctypes.c_int, _dp]
         L.orc_h_aca_block.argtypes = [ctypes.c_void_p, ctypes.c_long, ctypes.c_long, ctypes.c_long,
                                       ctypes.c_long, ctypes.c_double, ctypes.c_long, _dp, _dp, ctypes.c_int]
@@ -235,6 +236,14 @@ class HOracle:
         y = np.zeros_like(x)
         if lib().orc_h_matvec(self.h, _d(x), _d(y)) != 0:
             raise RuntimeError("not assembled")
+        return y
+
+    def lmatvec(self, x, trans=False):
+        """L~ x (or L~^T x) with the H-Cholesky factor, user order."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.zeros_like(x)
+        if lib().orc_h_lmatvec(self.h, int(bool(trans)), _d(x), _d(y)) != 0:
+            raise RuntimeError("not factored")
         return y
 
     def expand(self, which=0):

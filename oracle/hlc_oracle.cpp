@@ -1386,6 +1386,53 @@ int orc_h_matvec(void* h, const double* x, double* y) {
   return 0;
 }
 
+// y = L~ x (trans = 0) or y = L~^T x (trans = 1) with the H-Cholesky factor
+// L~ (the lower triangle of the factored block structure), in user order:
+// the plain definition y_i = sum_j L~_ij x_j, taken leaf block by leaf
+// block; a diagonal leaf contributes its lower triangle only.  Used to draw
+// synthetic data Z = L~ xi (Sec. 5.1).
+int orc_h_lmatvec(void* h, int trans, const double* x, double* y) {
+  HTree* T = static_cast<HTree*>(h);
+  if (!T->factored) return -3;
+  const long n = T->n;
+  std::vector<double> xt(n), yt(n, 0.0);
+  for (long i = 0; i < n; ++i) xt[i] = x[T->perm[i]];
+  std::vector<int> lv;
+  leaf_list(T->L, 0, lv);
+  for (int b : lv) {
+    const Block& bl = T->L[b];
+    const Cluster& cr = T->cl[bl.r];
+    const Cluster& cs = T->cl[bl.s];
+    const long m = cr.size(), nc = cs.size();
+    // rows of the block map to cr, columns to cs; transposed, the other way
+    const long in0 = trans ? cr.lo : cs.lo, out0 = trans ? cs.lo : cr.lo;
+    if (bl.type == DENSE) {
+      for (long j = 0; j < nc; ++j)
+        for (long i = 0; i < m; ++i) {
+          if (bl.diag && j > i) continue;
+          if (!trans)
+            yt[out0 + i] += bl.D(i, j) * xt[in0 + j];
+          else
+            yt[out0 + j] += bl.D(i, j) * xt[in0 + i];
+        }
+    } else {
+      const long k = bl.U.n;
+      for (long l = 0; l < k; ++l) {
+        double w = 0.0;
+        if (!trans) {
+          for (long j = 0; j < nc; ++j) w += bl.V(j, l) * xt[in0 + j];
+          for (long i = 0; i < m; ++i) yt[out0 + i] += bl.U(i, l) * w;
+        } else {
+          for (long i = 0; i < m; ++i) w += bl.U(i, l) * xt[in0 + i];
+          for (long j = 0; j < nc; ++j) yt[out0 + j] += bl.V(j, l) * w;
+        }
+      }
+    }
+  }
+  for (long i = 0; i < n; ++i) y[T->perm[i]] = yt[i];
+  return 0;
+}
+
 // Expand C~ (which = 0) or L~ (which = 1) to a dense n x n column-major
 // matrix in user order (small n only; C~ symmetric, L~ lower).
 int orc_h_expand(void* h, int which, double* out) {

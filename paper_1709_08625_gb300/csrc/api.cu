@@ -87,7 +87,8 @@ struct hlc_tree {
   double* d_knu = nullptr;  // 2 * KNU_NODES node table
   std::vector<double> h_knu;
   Plan chol, fwd, bwd, mv, recomp;
-  bool chol_ready = false, solve_ready = false;
+  Plan lmv, lmvt;  // products with the lower factor and its transpose
+  bool chol_ready = false, solve_ready = false, lmv_ready = false;
   double* d_tmp = nullptr;
   int64_t tmp_cap = 0;
   double* d_vec = nullptr;  // 6 n: W0 | X | Y | Z | XS | R
@@ -96,6 +97,10 @@ struct hlc_tree {
 };
 
 namespace {
+
+// largest n for the diagnostics that evaluate the exact covariance (O(n^2)
+// kernel evaluations per product)
+constexpr int64_t kDiagExactMax = 131072;
 
 int cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return HLC_OK;
@@ -541,7 +546,58 @@ int build_plans(hlc_tree* t, bool chol, bool solve) {
   }
   int64_t need = std::max(t->recomp.tmp_doubles, t->chol.tmp_doubles);
   need = std::max(need, std::max(t->fwd.tmp_doubles, std::max(t->bwd.tmp_doubles, t->mv.tmp_doubles)));
+  need = std::max(need, std::max(t->lmv.tmp_doubles, t->lmvt.tmp_doubles));
   return ensure_tmp(t, need);
+}
+
+// Plans of the products with the lower factor (in place on the vector at
+// offset 0 of the tree's vector workspace).
+int build_lmv_plans(hlc_tree* t) {
+  if (t->lmv_ready) return HLC_OK;
+  try {
+    plan_trmv(t->T, t->lmv, 0, 0, 1);
+    plan_trmv(t->T, t->lmvt, 1, 0, 1);
+    int st;
+    if ((st = check_plan(t, t->lmv)) || (st = check_plan(t, t->lmvt))) return st;
+    if ((st = upload_plan(t->lmv)) || (st = upload_plan(t->lmvt))) return st;
+  } catch (const std::bad_alloc&) {
+    return HLC_ERR_OOM;
+  } catch (const std::exception&) {
+    return HLC_ERR_CUDA;
+  }
+  t->lmv_ready = true;
+  return ensure_tmp(t, std::max(t->lmv.tmp_doubles, t->lmvt.tmp_doubles));
+}
+
+// y = L~ x (trans 0) or L~^T x (trans 1) in caller order, FP64 arithmetic;
+// x, y host or device.
+int factor_apply(hlc_tree* t, const hlc_hmat* L, int trans, const double* x, double* y) {
+  hlc_ctx* c = t->ctx;
+  int st = build_lmv_plans(t);
+  if (st) return st;
+  const int64_t n = t->T.n;
+  double* W0 = t->d_vec;
+  double* S = t->d_vec + 3 * n;  // staging
+  cudaStream_t s = c->stream;
+  if (is_device_ptr(x)) {
+    launch_gather(x, t->d_perm, W0, n, s);
+  } else {
+    CK(cudaMemcpyAsync(S, x, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_gather(S, t->d_perm, W0, n, s);
+  }
+  c->launches += 1;
+  Bases B = make_bases(t, L->arena, nullptr, L->ranks, false);
+  run_plan(t, trans ? t->lmvt : t->lmv, B, s);
+  if (is_device_ptr(y)) {
+    launch_scatter(W0, t->d_perm, y, n, s);
+  } else {
+    launch_scatter(W0, t->d_perm, S, n, s);
+    CK(cudaMemcpyAsync(y, S, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  }
+  c->launches += 1;
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  return take_status(c);
 }
 
 int do_assemble(hlc_tree* t, const hlc_theta* th, hlc_hmat* C) {
@@ -556,7 +612,8 @@ int do_assemble(hlc_tree* t, const hlc_theta* th, hlc_hmat* C) {
   // quadratic form z^T C~^-1 z inherits every perturbation of C~ amplified by
   // its condition number (FP32 ACA panels moved |dL|/n by ~5e-4 at
   // n = 524,288, ell = 0.0864, nugget 1e-4).
-  launch_aca(t->d_lr, (int64_t)t->T.lr_asm.size(), C->arena, t->d_px, t->d_py, mp, t->p.eps, C->ranks, c->stream);
+  launch_aca(t->d_lr, (int64_t)t->T.lr_asm.size(), C->arena, t->d_px, t->d_py, mp, t->p.eps, C->ranks,
+             c->d_status, c->stream);
   Bases B = make_bases(t, nullptr, C->arena, C->ranks, false);
   run_plan(t, t->recomp, B, c->stream);
   CK(cudaGetLastError());
@@ -581,6 +638,66 @@ int do_cholesky(hlc_tree* t, const hlc_hmat* C, hlc_hmat* L) {
   st = take_status(c);
   if (st == HLC_OK) L->valid = true;
   return st;
+}
+
+// Extreme eigenvalues of the symmetric tridiagonal matrix with diagonal d
+// and off-diagonal e (e[i] couples i and i+1) by bisection on the Sturm
+// sequence count (the number of eigenvalues below x is the number of
+// negative pivots of T - x I).
+int tridiag_count_below(const std::vector<double>& d, const std::vector<double>& e, double x) {
+  int cnt = 0;
+  double q = 1.0;
+  for (size_t i = 0; i < d.size(); ++i) {
+    const double off = i ? e[i - 1] * e[i - 1] : 0.0;
+    q = d[i] - x - (i ? off / q : 0.0);
+    if (q == 0.0) q = -1e-300;
+    if (q < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+void tridiag_extremes(const std::vector<double>& d, const std::vector<double>& e, double* lo, double* hi) {
+  double a = INFINITY, b = -INFINITY;
+  for (size_t i = 0; i < d.size(); ++i) {
+    const double r = (i ? fabs(e[i - 1]) : 0.0) + (i + 1 < d.size() ? fabs(e[i]) : 0.0);
+    a = std::min(a, d[i] - r);
+    b = std::max(b, d[i] + r);
+  }
+  const int k = (int)d.size();
+  for (int which = 0; which < 2; ++which) {
+    // which 0: smallest (count below x >= 1), 1: largest (count below x >= k)
+    double l = a, h = b;
+    for (int it = 0; it < 200 && h - l > 1e-15 * std::max(fabs(l), fabs(h)); ++it) {
+      const double m = 0.5 * (l + h);
+      if (tridiag_count_below(d, e, m) >= (which ? k : 1))
+        h = m;
+      else
+        l = m;
+    }
+    (which ? *hi : *lo) = 0.5 * (l + h);
+  }
+}
+
+// Estimate of |I - (L~ L~^T)^-1 C~|_2 from the preconditioned CG run (the
+// quantity of Table 5's last column).  CG with step lengths a_j and update
+// coefficients b_j is the Lanczos process of the preconditioned operator,
+// with tridiagonal T: T_00 = 1/a_0, T_jj = 1/a_j + b_{j-1}/a_{j-1},
+// T_{j-1,j} = sqrt(b_{j-1})/a_{j-1}.  The extreme eigenvalues of T (Ritz
+// values) approach those of the operator from inside, so the estimate is a
+// lower bound that tightens with the number of iterations.  -1 when no
+// iteration ran.
+double lanczos_rel_err(const std::vector<double>& al, const std::vector<double>& be) {
+  const size_t k = al.size();
+  if (k == 0) return -1.0;
+  std::vector<double> d(k), e(k > 1 ? k - 1 : 0);
+  for (size_t j = 0; j < k; ++j) {
+    if (!(al[j] > 0.0)) return -1.0;
+    d[j] = 1.0 / al[j] + (j ? be[j - 1] / al[j - 1] : 0.0);
+    if (j) e[j - 1] = sqrt(std::max(be[j - 1], 0.0)) / al[j - 1];
+  }
+  double lo = d[0], hi = d[0];
+  if (k > 1) tridiag_extremes(d, e, &lo, &hi);
+  return std::max(fabs(1.0 - lo), fabs(hi - 1.0));
 }
 
 double read_scalar(hlc_ctx* c, int idx) {
@@ -898,6 +1015,8 @@ void hlc_tree_free(hlc_tree* t) {
   free_plan(t->bwd);
   free_plan(t->mv);
   free_plan(t->recomp);
+  free_plan(t->lmv);
+  free_plan(t->lmvt);
   delete t;
 }
 
@@ -914,6 +1033,31 @@ int hlc_tree_info(const hlc_tree* t, int64_t* info) {
   info[5] = t->T.depth;
   info[6] = t->chol_ready ? t->chol.nops() : -1;
   info[7] = t->chol_ready ? t->chol.nwaves : -1;
+  return HLC_OK;
+}
+
+int hlc_tree_memory(const hlc_tree* t, int64_t* out) {
+  if (!t || !out) return HLC_ERR_ARG;
+  const HTree& T = t->T;
+  const int64_t arena = T.arena_doubles * 8 + (int64_t)T.nslots * 4;
+  const int64_t held = (t->wsC ? 1 : 0) + (t->wsL ? 1 : 0);
+  const int64_t tmp = t->tmp_cap * 8;
+  const int64_t vec = 6 * T.n * 8 + T.n * (4 + 16) + (int64_t)T.dense_asm.size() * sizeof(DenseAsm) +
+                      (int64_t)T.lr_asm.size() * sizeof(LrAsm) + t->ndiag * 12 + 2 * KNU_NODES * 8;
+  auto plan_bytes = [](const Plan& P) -> int64_t {
+    if (!P.checked) return 0;
+    return (int64_t)(P.gemm.size() * sizeof(OpGemm) + P.trsm.size() * sizeof(OpTrsm) +
+                     P.potrf.size() * sizeof(OpPotrf) + P.trunc.size() * sizeof(OpTrunc) +
+                     P.terms.size() * sizeof(TermD) + P.waves.size() * sizeof(WaveRange));
+  };
+  const int64_t plans = plan_bytes(t->chol) + plan_bytes(t->fwd) + plan_bytes(t->bwd) + plan_bytes(t->mv) +
+                        plan_bytes(t->recomp) + plan_bytes(t->lmv) + plan_bytes(t->lmvt);
+  out[0] = arena;
+  out[1] = held;
+  out[2] = tmp;
+  out[3] = vec;
+  out[4] = plans;
+  out[5] = arena * held + tmp + vec + plans;
   return HLC_OK;
 }
 
@@ -999,6 +1143,215 @@ int hlc_matvec(hlc_ctx* c, const hlc_hmat* C, const double* x, double* y) {
     CK(cudaMemcpyAsync(y, S, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   }
   CK(cudaStreamSynchronize(c->stream));
+  return take_status(c);
+}
+
+int hlc_factor_apply(hlc_ctx* c, const hlc_hmat* L, int trans, const double* x, double* y) {
+  if (!c || !L || !x || !y || L->which != 1 || L->t->ctx != c || (trans != 0 && trans != 1)) return HLC_ERR_ARG;
+  if (!L->valid) return HLC_ERR_STATE;
+  CK(cudaSetDevice(c->device));
+  return factor_apply(L->t, L, trans, x, y);
+}
+
+int hlc_sample(hlc_ctx* c, hlc_tree* t, const hlc_theta* th, const double* xi, double* z) {
+  if (!c || !t || !xi || !z || t->ctx != c || !valid_theta(th)) return HLC_ERR_ARG;
+  CK(cudaSetDevice(c->device));
+  int st = build_plans(t, true, false);
+  if (st) return st;
+  if (!t->wsC && (st = hmat_alloc(t, 0, &t->wsC))) return st;
+  if (!t->wsL && (st = hmat_alloc(t, 1, &t->wsL))) return st;
+  if ((st = do_assemble(t, th, t->wsC))) return st;
+  if ((st = do_cholesky(t, t->wsC, t->wsL))) return st;
+  return factor_apply(t, t->wsL, 0, xi, z);
+}
+
+// ---------------------------------------------------------------------------
+// Accuracy diagnostics (Sec. 3, Tables 2, 3 and 5)
+// ---------------------------------------------------------------------------
+namespace {
+
+// deterministic N(0, 1) draws on the host: SplitMix64 (Steele, Lea, Flood,
+// OOPSLA 2014) for uniforms, Box-Muller for the normals
+struct Probe {
+  uint64_t s;
+  uint64_t next() {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+  double uniform() { return ((next() >> 11) + 0.5) * (1.0 / 9007199254740992.0); }
+  void normals(std::vector<double>& v) {
+    for (size_t i = 0; i < v.size(); i += 2) {
+      const double r = sqrt(-2.0 * log(uniform())), a = 6.283185307179586 * uniform();
+      v[i] = r * cos(a);
+      if (i + 1 < v.size()) v[i + 1] = r * sin(a);
+    }
+  }
+};
+
+struct Diag {
+  hlc_tree* t;
+  hlc_ctx* c;
+  cudaStream_t s;
+  int64_t n;
+  MaternDev mp;
+  Bases BL, BC;
+  double *W0, *X, *Y;  // the tree's solve / matvec vectors (tree order)
+  double dot(const double* a, const double* b) {
+    launch_dot(a, b, n, c->d_part, c->d_scalar + 7, s);
+    c->launches += 2;
+    return read_scalar(c, 7);
+  }
+  void copy(double* d, const double* a) { cudaMemcpyAsync(d, a, n * sizeof(double), cudaMemcpyDeviceToDevice, s); }
+  void scale(double* v, double a) { launch_axpby(0.0, v, a, v, n, s); }
+  // out = C~ in
+  void hmv(double* out, const double* in) {
+    copy(X, in);
+    cudaMemsetAsync(Y, 0, n * sizeof(double), s);
+    run_plan(t, t->mv, BC, s);
+    copy(out, Y);
+  }
+  // out = C in (exact)
+  void xmv(double* out, const double* in) {
+    launch_exact_matvec(t->d_px, t->d_py, in, out, n, mp, s);
+    c->launches += 1;
+  }
+  // out = L~^-1 in (trans 0) or L~^-T in (trans 1)
+  void solve(double* out, const double* in, int trans) {
+    copy(W0, in);
+    run_plan(t, trans ? t->bwd : t->fwd, BL, s);
+    copy(out, W0);
+  }
+  // out = L~ in (trans 0) or L~^T in (trans 1)
+  void lmul(double* out, const double* in, int trans) {
+    copy(W0, in);
+    run_plan(t, trans ? t->lmvt : t->lmv, BL, s);
+    copy(out, W0);
+  }
+};
+
+}  // namespace
+
+int hlc_diagnostics(hlc_ctx* c, hlc_tree* t, const hlc_theta* th, int iters, int probes, uint64_t seed,
+                    double* out) {
+  if (!c || !t || !out || t->ctx != c || !valid_theta(th) || iters < 1 || iters > 1000 || probes < 0 ||
+      probes > 10000)
+    return HLC_ERR_ARG;
+  CK(cudaSetDevice(c->device));
+  for (int i = 0; i < 6; ++i) out[i] = -1.0;
+  int st = build_plans(t, true, true);
+  if (st) return st;
+  if ((st = build_lmv_plans(t))) return st;
+  if (!t->wsC && (st = hmat_alloc(t, 0, &t->wsC))) return st;
+  if (!t->wsL && (st = hmat_alloc(t, 1, &t->wsL))) return st;
+  if ((st = do_assemble(t, th, t->wsC))) return st;
+  if ((st = do_cholesky(t, t->wsC, t->wsL))) return st;
+  const int64_t n = t->T.n;
+  const bool exact = n <= kDiagExactMax;
+  Diag D;
+  D.t = t;
+  D.c = c;
+  D.s = c->stream;
+  D.n = n;
+  D.mp = matern_params(t, th);  // the node table is on the device since the assembly
+  // FP64 arithmetic throughout (the factor is stored in FP64 in every mode)
+  D.BL = make_bases(t, t->wsL->arena, nullptr, t->wsL->ranks, false);
+  D.BC = make_bases(t, nullptr, t->wsC->arena, t->wsC->ranks, false);
+  D.W0 = t->d_vec;
+  D.X = t->d_vec + n;
+  D.Y = t->d_vec + 2 * n;
+  double* buf = nullptr;
+  CK(cudaMalloc(&buf, 5 * n * sizeof(double)));
+  double *v = buf, *w = buf + n, *a = buf + 2 * n, *b = buf + 3 * n, *g = buf + 4 * n;
+  Probe rng{seed};
+  std::vector<double> h(n);
+  auto start = [&](double* dst) {
+    rng.normals(h);
+    cudaMemcpyAsync(dst, h.data(), n * sizeof(double), cudaMemcpyHostToDevice, D.s);
+    D.scale(dst, 1.0 / sqrt(D.dot(dst, dst)));
+  };
+  // power iteration on a symmetric operator: |A v_k| with v_k normalised
+  auto power = [&](auto&& apply) {
+    start(v);
+    double est = 0.0;
+    for (int k = 0; k < iters; ++k) {
+      apply(w, v);
+      est = sqrt(D.dot(w, w));
+      if (!(est > 0.0)) break;
+      D.copy(v, w);
+      D.scale(v, 1.0 / est);
+    }
+    return est;
+  };
+  // |C~ - L~ L~^T|_2 and |C~|_2
+  out[2] = power([&](double* o, const double* in) {
+    D.hmv(a, in);
+    D.lmul(b, in, 1);
+    D.lmul(o, b, 0);
+    launch_axpby(1.0, a, -1.0, o, n, D.s);  // o = C~ in - L L^T in
+  });
+  out[5] = power([&](double* o, const double* in) { D.hmv(o, in); });
+  // |I - (L~ L~^T)^-1 C~|_2: power iteration on A^T A with
+  // A = I - P^-1 C~, A^T = I - C~ P^-1, P = L~ L~^T
+  {
+    auto pinv = [&](double* o, const double* in) {
+      D.solve(b, in, 0);
+      D.solve(o, b, 1);
+    };
+    auto A = [&](double* o, const double* in) {
+      D.hmv(a, in);
+      pinv(o, a);
+      launch_axpby(1.0, in, -1.0, o, n, D.s);  // o = in - P^-1 C~ in
+    };
+    auto At = [&](double* o, const double* in) {
+      pinv(a, in);
+      D.hmv(o, a);
+      launch_axpby(1.0, in, -1.0, o, n, D.s);  // o = in - C~ P^-1 in
+    };
+    start(v);
+    double est = 0.0;
+    for (int k = 0; k < iters; ++k) {
+      A(g, v);
+      est = sqrt(D.dot(g, g));  // |A v|, v the current right singular vector estimate
+      At(w, g);
+      const double nw = sqrt(D.dot(w, w));
+      if (!(nw > 0.0)) break;
+      D.copy(v, w);
+      D.scale(v, 1.0 / nw);
+    }
+    out[3] = est;
+  }
+  if (exact) {
+    // |C - C~|_2 and |C|_2 with the exact covariance
+    out[0] = power([&](double* o, const double* in) {
+      D.xmv(o, in);
+      D.hmv(a, in);
+      launch_axpby(-1.0, a, 1.0, o, n, D.s);
+    });
+    out[1] = power([&](double* o, const double* in) { D.xmv(o, in); });
+    // KLD(C, C~) = 1/2 (tr(C~^-1 C) - n - log det(C~^-1 C)) = 1/2 sum (d_i - log(1 + d_i)) with d_i the
+    // eigenvalues of B = L~^-1 (C - C~) L~^-T; to second order 1/4 |B|_F^2, estimated with Gaussian probes
+    // (E |B g|^2 = |B|_F^2)
+    if (probes > 0) {
+      double acc = 0.0;
+      for (int p = 0; p < probes; ++p) {
+        rng.normals(h);
+        cudaMemcpyAsync(g, h.data(), n * sizeof(double), cudaMemcpyHostToDevice, D.s);
+        D.solve(v, g, 1);  // v = L^-T g
+        D.xmv(w, v);
+        D.hmv(a, v);
+        launch_axpby(-1.0, a, 1.0, w, n, D.s);  // w = (C - C~) v
+        D.solve(b, w, 0);
+        acc += D.dot(b, b);
+      }
+      out[4] = 0.25 * acc / probes;
+    }
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(D.s);
+  cudaFree(buf);
+  if (e != cudaSuccess) return cuda_status(e);
   return take_status(c);
 }
 
@@ -1126,6 +1479,7 @@ int hlc_loglik(hlc_ctx* c, hlc_tree* t, const hlc_theta* th, const double* z, hl
   launch_dot(R, R, n, c->d_part, c->d_scalar + 3, s);
   c->launches += 2;
   int it = 0;
+  std::vector<double> cg_alpha, cg_beta;  // CG step and update coefficients
   double rel = zn > 0.0 ? sqrt(read_scalar(c, 3)) / zn : 0.0;
   if (rel > t->p.refine_tol && t->p.refine_maxit > 0) {
     CK(cudaMemcpyAsync(W0, R, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -1140,6 +1494,7 @@ int hlc_loglik(hlc_ctx* c, hlc_tree* t, const hlc_theta* th, const double* z, hl
       launch_dot(X, Y, n, c->d_part, c->d_scalar + 6, s);
       c->launches += 2;
       const double alpha = rw / read_scalar(c, 6);
+      cg_alpha.push_back(alpha);
       launch_axpby(alpha, X, 1.0, XS, n, s);
       c->launches += 1;
       launch_axpby(-alpha, Y, 1.0, R, n, s);
@@ -1156,6 +1511,7 @@ int hlc_loglik(hlc_ctx* c, hlc_tree* t, const hlc_theta* th, const double* z, hl
       c->launches += 2;
       const double rw1 = read_scalar(c, 5);
       const double beta = rw1 / rw;
+      cg_beta.push_back(beta);
       rw = rw1;
       launch_axpby(1.0, W0, beta, X, n, s);
       c->launches += 1;  // p = w + beta p
@@ -1186,6 +1542,7 @@ int hlc_loglik(hlc_ctx* c, hlc_tree* t, const hlc_theta* th, const double* z, hl
   out->loglik = -0.5 * (double)n * log(2.0 * M_PI) - 0.5 * logdet - 0.5 * quad;
   out->refine_iters = it;
   out->rel_residual = rel;
+  out->est_rel_err = lanczos_rel_err(cg_alpha, cg_beta);
   out->ms_assemble = ms[0];
   out->ms_factor = ms[1];
   out->ms_solve = ms[2];
@@ -1275,15 +1632,24 @@ int hlc_matvec_noalloc(hlc_ctx* c, const hlc_hmat* C, const double* x, double* y
   Bases B = make_bases(t, nullptr, C->arena, C->ranks, false);
   B.buf[BUF_VEC] = S;
   B.buf[BUF_TMP] = S + 3 * n;
+  // the same choice as for every other plan run: one persistent launch when
+  // the context and the environment allow it and the cooperative launch is
+  // available, else the waves one launch at a time (neither allocates)
   const int md = (int)std::max<int64_t>(t->T.max_dense_dim, t->T.leaf);
-  if (launch_waves(t->mv.d_waves, (int)t->mv.waves.size(), t->mv.d_trsm, t->mv.d_gemm, B, c->d_gridbar, md,
-                   t->mv.tuned_per_sm, c->stream) != 0) {
-    cudaGetLastError();
-    return HLC_ERR_CUDA;
+  bool done = false;
+  if (c->persistent && !c->profiling && !g_prof.on && persistent_enabled()) {
+    if (launch_waves(t->mv.d_waves, (int)t->mv.waves.size(), t->mv.d_trsm, t->mv.d_gemm, B, c->d_gridbar, md,
+                     t->mv.tuned_per_sm, c->stream) == 0) {
+      done = true;
+      c->launches += 1;
+      c->persistent_launches += 1;
+    } else {
+      cudaGetLastError();
+    }
   }
+  if (!done) run_plan_launches(t, t->mv, B, c->stream, true);
   launch_scatter(S + 2 * n, t->d_perm, y, n, c->stream);
-  c->launches += 3;
-  c->persistent_launches += 1;
+  c->launches += 2;
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->stream));
   return take_status(c);

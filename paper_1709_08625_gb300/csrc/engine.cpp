@@ -748,6 +748,36 @@ struct Planner {
     trsv_t(L.ch[0], X0);
   }
 
+  // X := L X (L the lower factor): with L = [L11 0; L21 L22],
+  // X1 := L22 X1 + L21 X0 (X0 still unchanged), then X0 := L11 X0
+  void trmv(int32_t l, const PV& X) {
+    const Block& L = blk(l);
+    if (L.type == BT_DENSE) {
+      trsm(D(l), X, L.m, 2, dim(X.cols, X.dcol));
+      return;
+    }
+    const int64_t c = cut(l);
+    const PV X0 = rows(X, 0, c), X1 = rows(X, c, X.rows);
+    trmv(L.ch[3], X1);
+    hmul(L.ch[2], X0, X1, 1.0);
+    trmv(L.ch[0], X0);
+  }
+
+  // X := L^T X: X0 := L11^T X0 + L21^T X1 (X1 still unchanged), then
+  // X1 := L22^T X1
+  void trmv_t(int32_t l, const PV& X) {
+    const Block& L = blk(l);
+    if (L.type == BT_DENSE) {
+      trsm(D(l), X, L.m, 3, dim(X.cols, X.dcol));
+      return;
+    }
+    const int64_t c = cut(l);
+    const PV X0 = rows(X, 0, c), X1 = rows(X, c, X.rows);
+    trmv_t(L.ch[0], X0);
+    hmul_t(L.ch[2], X1, X0, 1.0);
+    trmv_t(L.ch[3], X1);
+  }
+
   // C += alpha U V^T
   void add_lr(int32_t c, const PV& Uv, const PV& Vv, Dim k, double alpha) {
     const Block& C = blk(c);
@@ -1105,6 +1135,20 @@ void plan_solve(HTree& T, Plan& P, int trans, int64_t voff, int64_t ncols) {
     pl.trsv_t(0, X);
   else
     pl.trsv(0, X);
+  pl.finish();
+}
+
+// In-place product of the lower factor (trans = 0: X := L X) or of its
+// transpose (trans = 1: X := L^T X) with the vector(s) in BUF_VEC at voff.
+void plan_trmv(HTree& T, Plan& P, int trans, int64_t voff, int64_t ncols) {
+  P = Plan();
+  Planner pl(T, P, BUF_L);
+  const int32_t v = pl.add_obj(BUF_VEC, voff, T.n);
+  PV X = pl.whole(v, T.n, ncols);
+  if (trans)
+    pl.trmv_t(0, X);
+  else
+    pl.trmv(0, X);
   pl.finish();
 }
 

@@ -39,6 +39,8 @@ void layout(HTree& T, int kmax);
 void plan_cholesky(HTree& T, Plan& P, bool accumulate = false);
 void plan_solve(HTree& T, Plan& P, int trans, int64_t voff, int64_t ncols);
 void plan_matvec(HTree& T, Plan& P, int64_t xoff, int64_t yoff, int64_t ncols);
+// X := L X (trans 0) or L^T X (trans 1), in place, L the lower factor
+void plan_trmv(HTree& T, Plan& P, int trans, int64_t voff, int64_t ncols);
 void plan_recompress(HTree& T, Plan& P);
 // Bounds check of every view against the buffer sizes (in doubles).
 std::string validate_plan(const Plan& P, const int64_t* bufsize);

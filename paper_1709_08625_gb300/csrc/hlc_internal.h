@@ -52,7 +52,8 @@ struct OpGemm {
   double alpha;
 };
 
-// X (n x c) := L^-1 X (trans = 0) or L^-T X (trans = 1); L dense lower n x n.
+// X (n x c) := L^-1 X (trans = 0), L^-T X (trans = 1), L X (trans = 2) or
+// L^T X (trans = 3); L dense lower n x n (its upper triangle is not read).
 struct OpTrsm {
   Mv L, X;
   int32_t n, trans;

@@ -61,24 +61,34 @@ __device__ __forceinline__ double aca_entry<double>(double x0, double y0, double
   return matern_f64(dist_f64(x0, y0, x1, y1), mp);
 }
 
+// Capacities of the per-block pivot bookkeeping: ranks up to ACA_KCAP
+// (the largest kmax a tree accepts), and every used row, including the
+// rows that were skipped as zero (at most 3 in a row per accepted pivot).
+constexpr int ACA_KCAP = 128;
+constexpr int ACA_ROWS = 4 * ACA_KCAP;
+
 template <class T>
 __global__ void __launch_bounds__(ACA_THREADS) k_aca(const LrAsm* blks, int64_t count, double* arena,
                                                       const double* px, const double* py, MaternDev mp,
-                                                      double eps, int* ranks) {
-  __shared__ double s_ui[64], s_vj[64];
-  __shared__ double s_cu[64][8], s_cv[64][8];
-  __shared__ int used_r[128], used_c[64];
+                                                      double eps, int* ranks, int* status) {
+  __shared__ double s_ui[ACA_KCAP], s_vj[ACA_KCAP];
+  __shared__ double s_cu[ACA_THREADS / 32][8], s_cv[ACA_THREADS / 32][8];
+  __shared__ int used_r[ACA_ROWS], used_c[ACA_KCAP];
   __shared__ double redv[33];
   __shared__ int redi[33];
   const int tid = threadIdx.x;
   for (int64_t o = blockIdx.x; o < count; o += gridDim.x) {
     const LrAsm b = blks[o];
-    const int m = b.m, n = b.n, kcap = b.kcap;
+    const int m = b.m, n = b.n;
+    // kcap > ACA_KCAP is refused when the tree is laid out; clamp anyway so
+    // that no index below can leave the shared arrays
+    const int kcap = b.kcap < ACA_KCAP ? b.kcap : ACA_KCAP;
     double* U = arena + b.offU;
     double* V = arena + b.offV;
     int k = 0, next = 0, zero_tries = 0, nur = 0, nuc = 0;
     double s2 = 0.0;
-    while (k < kcap && nur < 128) {
+    bool converged = false;
+    while (k < kcap && nur < ACA_ROWS) {
       const int i = next;
       __syncthreads();
       if (tid == 0) used_r[nur] = i;
@@ -103,9 +113,17 @@ __global__ void __launch_bounds__(ACA_THREADS) k_aca(const LrAsm* blks, int64_t 
       }
       double bval;
       const int jp = block_argmax(best, bj, redv, redi, &bval);
-      if (jp < 0) break;
+      if (jp < 0) {  // every column used: the approximant is exact
+        converged = true;
+        break;
+      }
       if (bval == 0.0) {
-        if (++zero_tries > 3) break;
+        // the residual vanishes on this row; after three such rows in a
+        // row the residual is taken to be zero (the stopping rule of ACA)
+        if (++zero_tries > 3) {
+          converged = true;
+          break;
+        }
         // first unused row
         int nx = -1;
         for (int t = 0; t < m && nx < 0; ++t) {
@@ -113,7 +131,10 @@ __global__ void __launch_bounds__(ACA_THREADS) k_aca(const LrAsm* blks, int64_t 
           for (int q = 0; q < nur; ++q) u |= (used_r[q] == t);
           if (!u) nx = t;
         }
-        if (nx < 0) break;
+        if (nx < 0) {  // every row used: exact
+          converged = true;
+          break;
+        }
         next = nx;
         continue;
       }
@@ -178,7 +199,10 @@ __global__ void __launch_bounds__(ACA_THREADS) k_aca(const LrAsm* blks, int64_t 
       }
       s2 += 2.0 * cross + uu * vv;
       ++k;
-      if (sqrt(uu) * sqrt(vv) <= eps * sqrt(fmax(s2, 0.0))) break;
+      if (sqrt(uu) * sqrt(vv) <= eps * sqrt(fmax(s2, 0.0))) {
+        converged = true;
+        break;
+      }
       // next pivot row: largest |u| among unused rows
       best = -1.0;
       int bi = -1;
@@ -192,11 +216,20 @@ __global__ void __launch_bounds__(ACA_THREADS) k_aca(const LrAsm* blks, int64_t 
         }
       }
       const int ip = block_argmax(best, bi, redv, redi, &bval);
-      if (ip < 0) break;
+      if (ip < 0) {
+        converged = true;
+        break;
+      }
       next = ip;
     }
     __syncthreads();
-    if (tid == 0) ranks[b.slot] = k;
+    // A block that reached its rank capacity before the stopping test held
+    // is not accurate to eps: reported as a rank overflow, unless the
+    // capacity is the full rank min(m, n), where the approximant is exact.
+    if (tid == 0) {
+      ranks[b.slot] = k;
+      if (!converged && k < (m < n ? m : n)) record_error(status, DEV_RANK, k);
+    }
     __syncthreads();
   }
 }
@@ -286,7 +319,27 @@ __device__ void do_trsm(const OpTrsm& op, const Bases& B, T* sL) {
       const int r = lane + 32 * q;
       x[q] = r < n ? (T)xc[r * op.X.rs] : T(0);
     }
-    if (!op.trans) {
+    if (op.trans >= 2) {
+      // multiplication by the lower triangle (trans 2) or its transpose
+      // (trans 3): y_r = sum_{i <= r} L_ri x_i, resp. sum_{i >= r} L_ir x_i,
+      // accumulated in a fixed order (increasing i)
+      T acc[4] = {T(0), T(0), T(0), T(0)};
+      for (int i = 0; i < n; ++i) {
+        const int owner = i & 31, qi = i >> 5;
+        const T mine = qi == 0 ? x[0] : qi == 1 ? x[1] : qi == 2 ? x[2] : x[3];
+        const T xi = __shfl_sync(0xffffffffu, mine, owner);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int r = lane + 32 * q;
+          if (r < n) {
+            if (op.trans == 2 && r >= i) acc[q] += sL[r + i * n] * xi;
+            if (op.trans == 3 && r <= i) acc[q] += sL[i + r * n] * xi;
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) x[q] = acc[q];
+    } else if (!op.trans) {
       for (int i = 0; i < n; ++i) {
         const int owner = i & 31, qi = i >> 5;
         T mine = qi == 0 ? x[0] : qi == 1 ? x[1] : qi == 2 ? x[2] : x[3];
@@ -580,6 +633,47 @@ int launch_waves(const WaveRange* waves, int nwaves, const OpTrsm* trsm, const O
 }
 
 // ---------------------------------------------------------------------------
+// Exact covariance matvec (accuracy diagnostics): y = C x with C_ij the
+// Matern function of eq. (3) plus the nugget on the diagonal, every entry
+// evaluated on the fly in FP64; one thread per row, the columns in tiles
+// staged in shared memory and summed in increasing order (deterministic).
+// ---------------------------------------------------------------------------
+constexpr int XMV_TILE = 256;
+
+__global__ void __launch_bounds__(XMV_TILE) k_exact_matvec(const double* px, const double* py, const double* x,
+                                                           double* y, int64_t n, MaternDev mp) {
+  __shared__ double sx[XMV_TILE], sy[XMV_TILE], sv[XMV_TILE];
+  for (int64_t r0 = (int64_t)blockIdx.x * XMV_TILE; r0 < n; r0 += (int64_t)gridDim.x * XMV_TILE) {
+    const int64_t i = r0 + threadIdx.x;
+    const double xi = i < n ? px[i] : 0.0, yi = i < n ? py[i] : 0.0;
+    double acc = 0.0;
+    for (int64_t c0 = 0; c0 < n; c0 += XMV_TILE) {
+      const int64_t j = c0 + threadIdx.x;
+      __syncthreads();
+      sx[threadIdx.x] = j < n ? px[j] : 0.0;
+      sy[threadIdx.x] = j < n ? py[j] : 0.0;
+      sv[threadIdx.x] = j < n ? x[j] : 0.0;
+      __syncthreads();
+      const int cnt = (int)(n - c0 < XMV_TILE ? n - c0 : XMV_TILE);
+      if (i < n)
+        for (int q = 0; q < cnt; ++q) {
+          double c = matern_f64(dist_f64(xi, yi, sx[q], sy[q]), mp);
+          if (c0 + q == i) c += mp.nugget;
+          acc += c * sv[q];
+        }
+    }
+    if (i < n) y[i] = acc;
+  }
+}
+
+void launch_exact_matvec(const double* px, const double* py, const double* x, double* y, int64_t n,
+                         const MaternDev& mp, cudaStream_t st) {
+  if (n <= 0) return;
+  const int64_t blocks = (n + XMV_TILE - 1) / XMV_TILE;
+  k_exact_matvec<<<(int)(blocks < 152 * 8 ? blocks : 152 * 8), XMV_TILE, 0, st>>>(px, py, x, y, n, mp);
+}
+
+// ---------------------------------------------------------------------------
 // small utilities
 // ---------------------------------------------------------------------------
 __global__ void k_gather(const double* src, const int32_t* perm, double* dst, int64_t n) {
@@ -650,9 +744,10 @@ void launch_dense_asm(const DenseAsm* d, int64_t count, double* arena, const dou
   k_dense_asm<<<grid_for(count, 152 * 16), 256, 0, st>>>(d, count, arena, px, py, mp);
 }
 void launch_aca(const LrAsm* d, int64_t count, double* arena, const double* px, const double* py,
-                const MaternDev& mp, double eps, int* ranks, cudaStream_t st) {
+                const MaternDev& mp, double eps, int* ranks, int* status, cudaStream_t st) {
   if (count <= 0) return;
-  k_aca<double><<<grid_for(count, 152 * 8), ACA_THREADS, 0, st>>>(d, count, arena, px, py, mp, eps, ranks);
+  k_aca<double><<<grid_for(count, 152 * 8), ACA_THREADS, 0, st>>>(d, count, arena, px, py, mp, eps, ranks,
+                                                                   status);
 }
 
 

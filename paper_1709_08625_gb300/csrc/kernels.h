@@ -15,8 +15,10 @@ int configure_kernels(int max_dense);
 
 void launch_dense_asm(const DenseAsm* d, int64_t count, double* arena, const double* px, const double* py,
                       const MaternDev& mp, cudaStream_t st);
+// ACA of every admissible leaf; a leaf that reaches its rank capacity before
+// the stopping test holds (and is not full rank) records DEV_RANK in status.
 void launch_aca(const LrAsm* d, int64_t count, double* arena, const double* px, const double* py,
-                const MaternDev& mp, double eps, int* ranks, cudaStream_t st);
+                const MaternDev& mp, double eps, int* ranks, int* status, cudaStream_t st);
 void launch_ops(int type, const void* ops, int64_t count, const TermD* terms, const Bases& B, int max_dense,
                 cudaStream_t st);
 // One cooperative launch executing all waves of a TRSM/GEMM plan with
@@ -28,6 +30,10 @@ int waves_max_per_sm(int max_dense);
 // Two CTAs wait at a grid barrier that expects one arrival more than the
 // grid has; the wait ends by its time limit with DEV_TIMEOUT in *status.
 int launch_barrier_probe(GridBar* gb, int* status, cudaStream_t st);
+// y = C x with the exact (dense, on the fly) covariance of the points in
+// tree order; O(n^2) kernel evaluations (accuracy diagnostics only)
+void launch_exact_matvec(const double* px, const double* py, const double* x, double* y, int64_t n,
+                         const MaternDev& mp, cudaStream_t st);
 void launch_gather(const double* src, const int32_t* perm, double* dst, int64_t n, cudaStream_t st);
 void launch_scatter(const double* src, const int32_t* perm, double* dst, int64_t n, cudaStream_t st);
 void launch_points(const double* xy, const int32_t* perm, double* px, double* py, int64_t n, cudaStream_t st);

@@ -37,29 +37,53 @@ struct Request {
   std::chrono::steady_clock::time_point t_submit;
 };
 
-struct Serve {
-  int device = 0;
+// The admission rule of the request loop, kept apart from the threads so
+// that it can be replayed on the host: the request at the head of the queue
+// is admitted when a slot is free and its footprint fits in what the budget
+// has left, or when nothing else is running (a request larger than the
+// whole budget then runs alone rather than never).  Arrival order is kept.
+struct Admission {
   size_t budget = 0;
   int max_slots = 1;
+  size_t in_use = 0;
+  int running = 0;
+  size_t peak = 0;
+  bool fits(size_t fp) const {
+    return running < max_slots && (in_use + fp <= budget || running == 0);
+  }
+  void admit(size_t fp) {
+    in_use += fp;
+    running += 1;
+    if (in_use > peak) peak = in_use;
+  }
+  void release(size_t fp) {
+    in_use -= fp;
+    running -= 1;
+  }
+};
+
+struct Serve {
+  int device = 0;
   std::mutex mu;
   std::condition_variable cv;
   std::deque<std::shared_ptr<Request>> queue;
   std::unordered_map<uint64_t, std::shared_ptr<Request>> all;
   uint64_t next_id = 1;
-  size_t in_use = 0;
+  Admission adm;
   bool stopping = false;
   std::vector<std::thread> workers;
   std::vector<hlc_ctx*> slot_ctx;
 };
 
 // Device footprint estimate of one evaluation before its tree exists: two
-// arenas (C~ and L~) of n (3 leaf + 7.5 log2(n / leaf) kcap) doubles -- the
-// dense near field plus low-rank panels whose summed row count grows like
-// n log n on uniform points -- plus temporaries and vectors.
+// arenas (C~ and L~) of n (3 leaf + 7.5 log2(n / leaf) kmax) doubles -- the
+// dense near field plus low-rank blocks of kmax columns whose summed row
+// count grows like n log n on uniform points -- plus temporaries and
+// vectors.  Low-rank blocks narrower than kmax reserve fewer columns, so the
+// estimate errs on the high side for small trees.
 size_t serve_footprint(int64_t n, const hlc_params& p) {
   const double lv = log2(fmax(2.0, (double)n / p.leaf));
-  const double kcap = p.kmax < 64 ? p.kmax : 64;
-  const double arena = 8.0 * n * (3.0 * p.leaf + 7.5 * lv * kcap);
+  const double arena = 8.0 * n * (3.0 * p.leaf + 7.5 * lv * p.kmax);
   return (size_t)(2.6 * arena + 64.0 * n + (64 << 20));
 }
 
@@ -78,13 +102,12 @@ void worker(hlc::Serve* S, int slot) {
       std::unique_lock<std::mutex> lk(S->mu);
       S->cv.wait(lk, [&] {
         if (S->queue.empty()) return S->stopping;
-        const size_t fp = S->queue.front()->footprint;
-        return S->in_use + fp <= S->budget || S->in_use == 0;
+        return S->adm.fits(S->queue.front()->footprint);
       });
       if (S->queue.empty()) return;  // stopping and drained
       r = S->queue.front();
       S->queue.pop_front();
-      S->in_use += r->footprint;
+      S->adm.admit(r->footprint);
     }
     hlc_tree* t = nullptr;
     hlc_result res{};
@@ -107,7 +130,7 @@ void worker(hlc::Serve* S, int slot) {
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - r->t_submit).count();
     {
       std::lock_guard<std::mutex> lk(S->mu);
-      S->in_use -= r->footprint;
+      S->adm.release(r->footprint);
       res.ms_total = ms;
       r->res = res;
       r->status = st;
@@ -127,8 +150,8 @@ int hlc_serve_start(hlc_ctx* ctx, size_t budget, int max_slots) {
   std::unique_ptr<hlc::Serve> s(new (std::nothrow) hlc::Serve());
   if (!s) return HLC_ERR_OOM;
   s->device = device_of(ctx);
-  s->budget = budget;
-  s->max_slots = max_slots;
+  s->adm.budget = budget;
+  s->adm.max_slots = max_slots;
   for (int i = 0; i < max_slots; ++i) {
     hlc_ctx* c = nullptr;
     const int st = hlc_create(&c, s->device);
@@ -186,6 +209,52 @@ int hlc_serve_poll(hlc_ctx* ctx, uint64_t req_id, hlc_result* out) {
   const int st = it->second->status;
   S->all.erase(it);
   return st;
+}
+
+size_t hlc_serve_footprint(int64_t n, const hlc_params* p) {
+  hlc_params q;
+  if (p)
+    q = *p;
+  else
+    hlc_default_params(&q);
+  if (n <= 0 || q.leaf < 1 || q.kmax < 1) return 0;
+  return serve_footprint(n, q);
+}
+
+int hlc_serve_admission_replay(size_t budget, int max_slots, int64_t nreq, const size_t* footprint,
+                               const double* duration, double* start, size_t* peak) {
+  if (budget == 0 || max_slots < 1 || nreq < 0 || (nreq > 0 && (!footprint || !duration || !start)) || !peak)
+    return HLC_ERR_ARG;
+  hlc::Admission adm;
+  adm.budget = budget;
+  adm.max_slots = max_slots;
+  struct Run {
+    double end;
+    size_t fp;
+  };
+  std::vector<Run> run;
+  double now = 0.0;
+  int64_t head = 0;
+  while (head < nreq || !run.empty()) {
+    // admit from the head of the queue while the rule allows
+    while (head < nreq && adm.fits(footprint[head])) {
+      if (!(duration[head] >= 0.0)) return HLC_ERR_ARG;
+      adm.admit(footprint[head]);
+      start[head] = now;
+      run.push_back(Run{now + duration[head], footprint[head]});
+      ++head;
+    }
+    if (run.empty()) break;  // cannot happen: an empty loop admits the head
+    // advance to the next completion
+    size_t first = 0;
+    for (size_t i = 1; i < run.size(); ++i)
+      if (run[i].end < run[first].end) first = i;
+    now = run[first].end;
+    adm.release(run[first].fp);
+    run.erase(run.begin() + (std::ptrdiff_t)first);
+  }
+  *peak = adm.peak;
+  return HLC_OK;
 }
 
 int hlc_serve_stop(hlc_ctx* ctx) {

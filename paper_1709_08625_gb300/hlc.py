@@ -46,12 +46,27 @@ class hlc_params(ctypes.Structure):
 class hlc_result(ctypes.Structure):
     _fields_ = [("loglik", ctypes.c_double), ("logdet", ctypes.c_double), ("quad", ctypes.c_double),
                 ("quad_factor", ctypes.c_double), ("refine_iters", ctypes.c_int),
-                ("rel_residual", ctypes.c_double), ("bytes_C", ctypes.c_size_t), ("bytes_L", ctypes.c_size_t),
+                ("rel_residual", ctypes.c_double), ("est_rel_err", ctypes.c_double),
+                ("bytes_C", ctypes.c_size_t), ("bytes_L", ctypes.c_size_t),
                 ("max_rank_C", ctypes.c_int), ("max_rank_L", ctypes.c_int), ("ms_assemble", ctypes.c_double),
                 ("ms_factor", ctypes.c_double), ("ms_solve", ctypes.c_double), ("ms_total", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class hlc_fit_opts(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_double * 3), ("size_tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("free_mask", ctypes.c_int)]
+
+
+class hlc_fit_result(ctypes.Structure):
+    _fields_ = [("theta", hlc_theta), ("loglik", ctypes.c_double), ("iterations", ctypes.c_int),
+                ("evaluations", ctypes.c_int), ("failed_evals", ctypes.c_int), ("converged", ctypes.c_int),
+                ("traced", ctypes.c_int), ("ms_total", ctypes.c_double)]
+
+
+OBJECTIVE = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p)
 
 
 class HlcError(RuntimeError):
@@ -95,6 +110,19 @@ _SIGS = {
                                         ctypes.POINTER(ctypes.c_uint64)]),
     "hlc_serve_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(hlc_result)]),
     "hlc_serve_stop": (ctypes.c_int, [_vp]),
+    "hlc_serve_footprint": (ctypes.c_size_t, [_i64, ctypes.POINTER(hlc_params)]),
+    "hlc_serve_admission_replay": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, _i64, _vp, _vp, _vp,
+                                                  ctypes.POINTER(ctypes.c_size_t)]),
+    "hlc_tree_memory": (ctypes.c_int, [_vp, _vp]),
+    "hlc_factor_apply": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _vp]),
+    "hlc_nelder_mead": (ctypes.c_int, [ctypes.c_int, _vp, _vp, ctypes.c_double, ctypes.c_int, OBJECTIVE, _vp, _vp,
+                                       _vp]),
+    "hlc_default_fit_opts": (None, [ctypes.POINTER(hlc_fit_opts)]),
+    "hlc_fit": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(hlc_theta), ctypes.POINTER(hlc_fit_opts), _vp,
+                               ctypes.c_int, ctypes.POINTER(hlc_fit_result)]),
+    "hlc_sample": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(hlc_theta), _vp, _vp]),
+    "hlc_diagnostics": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(hlc_theta), ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_uint64, _vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -146,6 +174,58 @@ def params(leaf=64, eta=2.0, eps=1e-6, precision=HLC_FP64, refine_tol=1e-12, ref
 
 def theta(sigma2, ell, nu, nugget):
     return hlc_theta(float(sigma2), float(ell), float(nu), float(nugget))
+
+
+def nelder_mead(f, x0, step, size_tol=1e-5, max_iter=200):
+    """hlc_nelder_mead with a Python objective f(x: ndarray) -> float;
+    returns (x, fmin, iterations)."""
+    x = np.array(x0, dtype=np.float64)
+    st = np.ascontiguousarray(step, dtype=np.float64)
+    d = x.size
+
+    def cb(p, _):
+        return float(f(np.ctypeslib.as_array(p, shape=(d,)).copy()))
+
+    c = OBJECTIVE(cb)
+    fmin = ctypes.c_double()
+    it = ctypes.c_int()
+    _check(hlc_nelder_mead(d, _ptr(x), _ptr(st), float(size_tol), int(max_iter), c, None, ctypes.byref(fmin),
+                           ctypes.byref(it)), "hlc_nelder_mead")
+    return x, fmin.value, it.value
+
+
+def fit_opts(step=None, size_tol=None, max_iter=None, free_mask=None):
+    o = hlc_fit_opts()
+    hlc_default_fit_opts(ctypes.byref(o))
+    if step is not None:
+        for i in range(3):
+            o.step[i] = float(step[i])
+    if size_tol is not None:
+        o.size_tol = float(size_tol)
+    if max_iter is not None:
+        o.max_iter = int(max_iter)
+    if free_mask is not None:
+        o.free_mask = int(free_mask)
+    return o
+
+
+def serve_footprint(n, **kw):
+    """Bytes the request loop charges for one request of n points."""
+    p = params(**kw)
+    return int(hlc_serve_footprint(int(n), ctypes.byref(p)))
+
+
+def admission_replay(budget, max_slots, footprints, durations):
+    """Host-only replay of the serve loop's admission rule: returns the
+    admission times of the requests (queued at time 0 in order) and the
+    peak sum of footprints running at once."""
+    fp = np.ascontiguousarray(footprints, dtype=np.uint64)
+    du = np.ascontiguousarray(durations, dtype=np.float64)
+    start = np.zeros(fp.size)
+    peak = ctypes.c_size_t()
+    _check(hlc_serve_admission_replay(int(budget), int(max_slots), fp.size, _ptr(fp), _ptr(du), _ptr(start),
+                                      ctypes.byref(peak)), "hlc_serve_admission_replay")
+    return start, int(peak.value)
 
 
 class Context:
@@ -245,6 +325,14 @@ class HMat:
         _check(hlc_matvec(self.ctx.h, self.h, _ptr(x), _ptr(y)), "hlc_matvec")
         return y
 
+    def factor_apply(self, x, trans=False, y=None):
+        """y = L~ x (or L~^T x) with this factor (from Tree.cholesky)."""
+        if y is None:
+            x = np.ascontiguousarray(x, dtype=np.float64)
+            y = np.empty_like(x)
+        _check(hlc_factor_apply(self.ctx.h, self.h, int(bool(trans)), _ptr(x), _ptr(y)), "hlc_factor_apply")
+        return y
+
     def matvec_noalloc(self, x, y):
         """y = C~ x into the caller's device tensor y (x, y on the device)."""
         _check(hlc_matvec_noalloc(self.ctx.h, self.h, _ptr(x), _ptr(y)), "hlc_matvec_noalloc")
@@ -283,6 +371,12 @@ class Tree:
         return dict(n=int(a[0]), clusters=int(a[1]), leaf_clusters=int(a[2]), dense=int(a[3]),
                     lowrank=int(a[4]), depth=int(a[5]), plan_ops=int(a[6]), plan_waves=int(a[7]))
 
+    def memory(self):
+        a = np.zeros(6, dtype=np.int64)
+        _check(hlc_tree_memory(self.h, _ptr(a)), "hlc_tree_memory")
+        return dict(arena=int(a[0]), matrices=int(a[1]), tmp=int(a[2]), vectors=int(a[3]), plans=int(a[4]),
+                    total=int(a[5]))
+
     def perm(self):
         p = np.zeros(self.n, dtype=np.int32)
         _check(hlc_tree_perm(self.h, _ptr(p)), "hlc_tree_perm")
@@ -302,6 +396,36 @@ class Tree:
         h = _vp()
         _check(hlc_cholesky(self.ctx.h, C.h, ctypes.byref(h)), "hlc_cholesky")
         return HMat(self.ctx, self, h)
+
+    def sample(self, th, xi, z=None):
+        """z = L~(theta) xi, synthetic data from the H-Cholesky factor (Sec. 5.1)."""
+        if not hasattr(xi, "data_ptr"):
+            xi = np.ascontiguousarray(xi, dtype=np.float64)
+        if z is None:
+            z = np.empty(self.n) if not hasattr(xi, "data_ptr") else xi.new_empty(self.n)
+        _check(hlc_sample(self.ctx.h, self.h, ctypes.byref(th), _ptr(xi), _ptr(z)), "hlc_sample")
+        return z
+
+    def fit(self, z, start, trace_cap=0, **opts):
+        """Nelder-Mead identification of (nu, ell, sigma2) (hlc_fit); returns
+        (result dict, trace array of {nu, ell, sigma2, loglik, status} rows)."""
+        if not hasattr(z, "data_ptr"):
+            z = np.ascontiguousarray(z, dtype=np.float64)
+        o = fit_opts(**opts)
+        tr = np.zeros((max(trace_cap, 0), 5))
+        r = hlc_fit_result()
+        _check(hlc_fit(self.ctx.h, self.h, _ptr(z), ctypes.byref(start), ctypes.byref(o),
+                       _ptr(tr) if trace_cap > 0 else None, int(trace_cap), ctypes.byref(r)), "hlc_fit")
+        out = {k: getattr(r, k) for k, _ in r._fields_ if k != "theta"}
+        out.update(sigma2=r.theta.sigma2, ell=r.theta.ell, nu=r.theta.nu, nugget=r.theta.nugget)
+        return out, tr[: r.traced]
+
+    def diagnostics(self, th, iters=20, probes=16, seed=1):
+        """hlc_diagnostics: dict of the norm and KLD estimates (-1: not computed)."""
+        a = np.zeros(6)
+        _check(hlc_diagnostics(self.ctx.h, self.h, ctypes.byref(th), int(iters), int(probes), int(seed), _ptr(a)),
+               "hlc_diagnostics")
+        return dict(err_C=a[0], norm_C=a[1], err_LLt=a[2], inv_err=a[3], kld=a[4], norm_Ch=a[5])
 
     def loglik(self, th, z):
         if not hasattr(z, "data_ptr"):

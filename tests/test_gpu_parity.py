@@ -208,12 +208,10 @@ def test_large_blocks_vs_h_oracle(ctx, hlc, nu):
 
 
 @pytest.mark.parametrize("n,nu,eps", [(5000, 0.5, 1e-6), (12000, 0.5, 1e-5), (8000, 0.325, 1e-6),
-                                      (16384, 0.5, 1e-7)])
+                                      (16384, 0.5, 1e-7), (12000, 1.5, 1e-6)])
 def test_mixed_vs_fp64(ctx, hlc, n, nu, eps):
-    # The FP32 panels of the mixed mode meet the 1e-6 bar for the exponential
-    # and rough kernels; for nu = 3/2 with tau^2 = 1e-4 the covariance is too
-    # ill-conditioned for FP32 panels (|dL|/n ~ 7e-2 at n = 12,000), and
-    # HLC_FP64 is the mode to use there.
+    # mixed (FP32 panels, products and recompression core; FP64 assembly,
+    # leaf POTRF, log det and PCG residual) against the plain FP64 path
     xy = inputs.points(n, 1200 + n)
     z = inputs.normal(n, 1300 + n)
     th = hlc.theta(1.0, 0.05, nu, 1e-4)
@@ -222,6 +220,32 @@ def test_mixed_vs_fp64(ctx, hlc, n, nu, eps):
     assert rmx["rel_residual"] <= 1e-10
     assert abs(rmx["loglik"] - r64["loglik"]) / n <= 1e-6
     assert abs(rmx["logdet"] - r64["logdet"]) / n <= 1e-6
+    assert abs(rmx["quad"] - r64["quad"]) / n <= 1e-6
+
+
+@pytest.mark.parametrize("nu", [1.5, 0.325])
+def test_n65536_vs_h_oracle_fp64_and_mixed(hlc, nu):
+    # The n = 65,536 workloads (l = 0.05, eps = 1e-6, leaf 64, z ~ N(0, I)):
+    # the GPU in HLC_FP64 and in HLC_MIXED against one CPU H-oracle
+    # evaluation, element-wise on log det and the quadratic form.  Bars per
+    # location: 1e-7 in FP64 (the same H-arithmetic; truncation decisions at
+    # the eps threshold may round differently), 1e-6 in mixed.
+    name = f"n65536_nu{nu}_eps1e-6"
+    w = inputs.WORKLOADS[name]
+    xy = inputs.workload_points(name)
+    z = inputs.workload_normal(name)
+    n = w["n"]
+    th = (w["sigma2"], w["ell"], w["nu"], w["nugget"])
+    ho = oracle.h_loglik(xy, z, *th, w["eps"], leaf=w["leaf"], eta=w["eta"])
+    c = hlc.Context(0)
+    for prec, bar in ((hlc.HLC_FP64, 1e-7), (hlc.HLC_MIXED, 1e-6)):
+        t = c.build_tree(xy, leaf=w["leaf"], eta=w["eta"], eps=w["eps"], precision=prec)
+        r = t.loglik(hlc.theta(*th), z)
+        for k in ("loglik", "logdet", "quad"):
+            assert abs(r[k] - ho[k]) / n <= bar, (prec, k, r[k], ho[k])
+        assert r["rel_residual"] <= 1e-10
+        t.free()
+    c.close()
 
 
 @pytest.mark.parametrize("n,nu,eps", [(12000, 0.5, 1e-5), (16384, 0.5, 1e-7)])

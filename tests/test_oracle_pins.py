@@ -431,3 +431,44 @@ def test_h_loglik_permutation_invariance():
     r1 = oracle.h_loglik(xy[p], z[p], 1.0, 0.08, 0.5, 1e-4, 1e-7, leaf=32)
     assert abs(r1["loglik"] - r0["loglik"]) <= 1e-9 * abs(r0["loglik"])
     assert abs(r1["logdet"] - r0["logdet"]) <= 1e-9 * abs(r0["logdet"])
+
+
+# ----------------------------------------------------------------------------
+# Products with the H-Cholesky factor (synthetic data Z = L~ xi, Sec. 5.1)
+# ----------------------------------------------------------------------------
+def test_factor_product_equals_dense_cholesky_of_tree_ordered_matrix():
+    # At an accuracy below rounding every low-rank block is exact, so the
+    # H-Cholesky factor is the dense Cholesky factor of the covariance in
+    # tree order: L~ x (user order) = P L_p P^T x with L_p = chol(P^T C P).
+    n = 400
+    xy = inputs.points(n, 4100)
+    th = (1.0, 0.1, 0.5, 1e-2)
+    H = oracle.HOracle(xy, leaf=32)
+    H.assemble(*th, 1e-15)
+    H.cholesky(1e-15)
+    perm = H.perm()
+    C = oracle.dense_cov(xy, *th)
+    Lp = np.linalg.cholesky(C[np.ix_(perm, perm)])
+    x = inputs.normal(n, 4101)
+    for trans in (False, True):
+        A = Lp.T if trans else Lp
+        ref = np.zeros(n)
+        ref[perm] = A @ x[perm]
+        got = H.lmatvec(x, trans=trans)
+        assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+def test_factor_product_reproduces_covariance():
+    # L~ (L~^T x) = C~ x to the accuracy of the factorisation (order eps)
+    n, eps = 2500, 1e-8
+    xy = inputs.points(n, 4102)
+    H = oracle.HOracle(xy, leaf=32)
+    H.assemble(1.0, 0.08, 1.5, 1e-4, eps)
+    H.cholesky(eps)
+    x = inputs.normal(n, 4103)
+    y = H.lmatvec(H.lmatvec(x, trans=True))
+    ref = H.matvec(x)
+    assert np.linalg.norm(y - ref) <= 50 * eps * np.linalg.norm(ref)
+    # and against the expanded factor (the lower triangle of the blocks)
+    Le = H.expand(1)
+    np.testing.assert_allclose(H.lmatvec(x), Le @ x, rtol=0, atol=1e-12 * np.abs(Le @ x).max())
