@@ -775,27 +775,26 @@ void flush(HCtx& H, int b) {
   add_terms(H, b, terms);
 }
 
-// Truncated sum C := trunc(C + sum_t U_t V_t^T) for a low-rank target
-// (the truncated addition of Table 1).  Terms are added in batches of at most
-// kTruncBatch new columns: acc := trunc(acc + batch), so that every core SVD
-// stays small.
+// Truncated sum (U, V) := trunc(U V^T + sum_t U_t V_t^T) of an m x n low-rank
+// matrix (the truncated addition of Table 1), term by term in order: terms
+// are taken in batches of at most kTruncBatch new columns (and at most 64
+// terms; a wider term forms a batch of its own), acc := trunc(acc + batch),
+// so that every core SVD stays small.  An empty (U, V) starts from zero.
 constexpr long kTruncBatch = 64;
 
-void add_terms(HCtx& H, int c, std::vector<Term>& terms) {
-  Block& C = H.b(c);
-  const long m = H.rows(c), n = H.cols(c);
+void trunc_sum(Mat& CU, Mat& CV, long m, long n, const std::vector<Term>& terms, double eps) {
   size_t t0 = 0;
   while (t0 < terms.size()) {
     size_t t1 = t0;
     long kb = 0;
     while (t1 < terms.size() && (kb == 0 || kb + terms[t1].U.n <= kTruncBatch) && t1 - t0 < 64)
       kb += terms[t1++].U.n;
-    const long K = C.U.n + kb;
+    const long K = CU.n + kb;
     Mat U(m, K), V(n, K);
     long col = 0;
-    for (long l = 0; l < C.U.n; ++l, ++col) {
-      for (long i = 0; i < m; ++i) U(i, col) = C.U(i, l);
-      for (long i = 0; i < n; ++i) V(i, col) = C.V(i, l);
+    for (long l = 0; l < CU.n; ++l, ++col) {
+      for (long i = 0; i < m; ++i) U(i, col) = CU(i, l);
+      for (long i = 0; i < n; ++i) V(i, col) = CV(i, l);
     }
     for (size_t q = t0; q < t1; ++q) {
       const Term& t = terms[q];
@@ -804,11 +803,63 @@ void add_terms(HCtx& H, int c, std::vector<Term>& terms) {
         for (long i = 0; i < t.V.m; ++i) V(t.coff + i, col) = t.V(i, l);
       }
     }
-    truncate_lr(U, V, H.eps);
-    C.U = std::move(U);
-    C.V = std::move(V);
+    truncate_lr(U, V, eps);
+    CU = std::move(U);
+    CV = std::move(V);
     t0 = t1;
   }
+}
+
+// Truncated sum of many terms into a low-rank block C (Table 1's truncated
+// addition, applied to a sum whose order the paper leaves open).  Up to
+// kTreeMinTerms - 1 terms are added in order (trunc_sum).  With more, the
+// sum is formed as a balanced tree: the terms are split in order into
+// groups of kTreeLeafTerms, each group is truncated on its own (S_g :=
+// trunc(sum of the group)), adjacent partial sums are combined pairwise
+// (S := trunc(S_a + S_b); an odd last one moves up unchanged) until two
+// remain, and C := trunc(C + S_1 + S_2).  Every node truncates at eps; the
+// grouping depends on the number of terms only.
+constexpr size_t kTreeMinTerms = 9;
+constexpr size_t kTreeLeafTerms = 4;
+
+void add_terms(HCtx& H, int c, std::vector<Term>& terms) {
+  Block& C = H.b(c);
+  const long m = H.rows(c), n = H.cols(c);
+  if (terms.size() < kTreeMinTerms) {
+    trunc_sum(C.U, C.V, m, n, terms, H.eps);
+    return;
+  }
+  std::vector<Term> level;
+  for (size_t g = 0; g < terms.size(); g += kTreeLeafTerms) {
+    const size_t e = std::min(terms.size(), g + kTreeLeafTerms);
+    std::vector<Term> grp(terms.begin() + g, terms.begin() + e);
+    Term s;
+    s.U = Mat(m, 0);
+    s.V = Mat(n, 0);
+    s.roff = s.coff = 0;
+    trunc_sum(s.U, s.V, m, n, grp, H.eps);
+    level.push_back(std::move(s));
+  }
+  while (level.size() > 2) {
+    std::vector<Term> next;
+    for (size_t i = 0; i < level.size(); i += 2) {
+      if (i + 1 == level.size()) {
+        next.push_back(std::move(level[i]));
+        break;
+      }
+      std::vector<Term> pair;
+      pair.push_back(std::move(level[i]));
+      pair.push_back(std::move(level[i + 1]));
+      Term s;
+      s.U = Mat(m, 0);
+      s.V = Mat(n, 0);
+      s.roff = s.coff = 0;
+      trunc_sum(s.U, s.V, m, n, pair, H.eps);
+      next.push_back(std::move(s));
+    }
+    level.swap(next);
+  }
+  trunc_sum(C.U, C.V, m, n, level, H.eps);
 }
 
 // C += U V^T (with truncation when C is low-rank).
