@@ -41,6 +41,9 @@
  *                     as one cooperative launch
  *   HLC_GRAPHS=0      launch the op waves directly instead of replaying CUDA
  *                     graphs
+ *   HLC_CHAINS=0      plan the solves of small diagonal blocks op by op
+ *                     instead of as chains run by one CTA each (same result,
+ *                     bit for bit)
  *   HLC_HOST_TREE=1   build the cluster and block trees on the host
  *   HLC_PROFILE=1     time every op launch (synchronising) and print a summary
  *                     at exit
@@ -341,10 +344,12 @@ int hlc_ctx_set_profiling(hlc_ctx* ctx, int on);
 /* Counters since the last reset (reset = 1 clears them after reading):
  * out[0] kernel launches of the library,
  * out[1 + 3*t .. 3 + 3*t] for op type t in {0 potrf, 1 trsm, 2 gemm,
- *   3 truncation (one CTA), 4 truncation (cluster)}: launches, device ms
- *   (profiling on), algorithmic flops,
- * out[16] launches of the persistent solve kernel (one per triangular solve
- *   or matvec; their TRSM/GEMM ops are not counted per type).  17 doubles. */
+ *   3 truncation (one CTA), 4 truncation (cluster), 5 chain (a small
+ *   diagonal block's solve run by one CTA)}: launches, device ms (profiling
+ *   on), algorithmic flops (chains: counted under trsm and gemm),
+ * out[19] launches of the persistent solve kernel (one per triangular solve,
+ *   product with the factor or matvec; their ops are not counted per type).
+ * 20 doubles. */
 int hlc_ctx_counters(hlc_ctx* ctx, int reset, double* out);
 
 /* ---- serving: continuous batching of likelihood requests ------------------ */

@@ -134,24 +134,28 @@ int upload(T** d, const std::vector<T>& h) {
   return HLC_OK;
 }
 
-// Wave table of a plan made of TRSM and GEMM ops only (solves, matvec).
+// Wave table of a plan made of TRSM, GEMM and chain ops only (solves,
+// products with the factor, matvec).
 void build_waves(Plan& P) {
   P.waves.clear();
   for (const Launch& L : P.launches)
-    if (L.type != OP_TRSM && L.type != OP_GEMM) return;
+    if (L.type != OP_TRSM && L.type != OP_GEMM && L.type != OP_CHAIN) return;
   int32_t cur = -1;
   for (const Launch& L : P.launches) {
     if (L.wave != cur) {
-      P.waves.push_back(WaveRange{0, 0, 0, 0});
+      P.waves.push_back(WaveRange{0, 0, 0, 0, 0, 0});
       cur = L.wave;
     }
     WaveRange& w = P.waves.back();
     if (L.type == OP_TRSM) {
       w.trsm0 = L.first;
       w.ntrsm = L.count;
-    } else {
+    } else if (L.type == OP_GEMM) {
       w.gemm0 = L.first;
       w.ngemm = L.count;
+    } else {
+      w.chain0 = L.first;
+      w.nchain = L.count;
     }
   }
 }
@@ -166,6 +170,10 @@ int upload_plan(Plan& P) {
   if ((st = upload(&P.d_potrf, P.potrf))) return st;
   if ((st = upload(&P.d_trunc, P.trunc))) return st;
   if ((st = upload(&P.d_terms, P.terms))) return st;
+  if ((st = upload(&P.d_chain, P.chain))) return st;
+  if ((st = upload(&P.d_citems, P.citems))) return st;
+  if ((st = upload(&P.d_ctrsm, P.ctrsm))) return st;
+  if ((st = upload(&P.d_cgemm, P.cgemm))) return st;
   return HLC_OK;
 }
 
@@ -179,6 +187,14 @@ void free_plan(Plan& P) {
   cudaFree(P.d_potrf);
   cudaFree(P.d_trunc);
   cudaFree(P.d_terms);
+  cudaFree(P.d_chain);
+  cudaFree(P.d_citems);
+  cudaFree(P.d_ctrsm);
+  cudaFree(P.d_cgemm);
+  P.d_chain = nullptr;
+  P.d_citems = nullptr;
+  P.d_ctrsm = nullptr;
+  P.d_cgemm = nullptr;
   P.d_gemm = nullptr;
   P.d_trsm = nullptr;
   P.d_potrf = nullptr;
@@ -212,7 +228,7 @@ struct Prof {
   Prof() { on = getenv("HLC_PROFILE") && getenv("HLC_PROFILE")[0] == '1'; }
   ~Prof() {
     if (!on) return;
-    static const char* nm[NOPTYPES] = {"potrf", "trsm", "gemm", "trunc", "truncC"};
+    static const char* nm[NOPTYPES] = {"potrf", "trsm", "gemm", "trunc", "truncC", "chain"};
     for (int i = 0; i < NOPTYPES; ++i)
       fprintf(stderr, "hlc-profile %-6s launches %9lld ops %11lld  %10.2f ms\n", nm[i], (long long)launches[i],
               (long long)ops[i], ms[i]);
@@ -236,6 +252,13 @@ void run_launch(hlc_tree* t, const Plan& P, const Bases& B, const Launch& L, int
 // CTAs per SM tried by the grid tuning of the persistent kernel (capped at
 // what fits on an SM when launched)
 constexpr int kTuneCandidates[3] = {1, 2, 4};
+
+// solves and products with the factor as chains of small diagonal blocks
+// (HLC_CHAINS=0: one op per wave step throughout)
+bool chains_enabled() {
+  static const bool on = !(getenv("HLC_CHAINS") && getenv("HLC_CHAINS")[0] == '0');
+  return on;
+}
 
 bool persistent_enabled() {
   static const bool on = !(getenv("HLC_PERSISTENT") && getenv("HLC_PERSISTENT")[0] == '0');
@@ -271,7 +294,8 @@ void run_plan(hlc_tree* t, const Plan& P, const Bases& B, cudaStream_t st) {
       }
       if (e0 && e1) cudaEventRecord(e0, st);
     }
-    if (launch_waves(P.d_waves, (int)P.waves.size(), P.d_trsm, P.d_gemm, B, c->d_gridbar, md, per, st) == 0) {
+    if (launch_waves(P.d_waves, (int)P.waves.size(), P.d_trsm, P.d_gemm, P.d_chain, P.chains(), B, c->d_gridbar, md,
+                     per, st) == 0) {
       c->launches += 1;
       c->persistent_launches += 1;
       if (cand >= 0) {
@@ -367,6 +391,7 @@ void run_launch(hlc_tree* t, const Plan& P, const Bases& B, const Launch& L, int
       case OP_GEMM: ops = P.d_gemm + L.first; break;
       case OP_TRSM: ops = P.d_trsm + L.first; break;
       case OP_POTRF: ops = P.d_potrf + L.first; break;
+      case OP_CHAIN: ops = P.d_chain + L.first; break;
       default: ops = P.d_trunc + L.first; break;  // OP_TRUNC, OP_TRUNC_BIG
     }
     hlc_ctx* c = t->ctx;
@@ -382,18 +407,18 @@ void run_launch(hlc_tree* t, const Plan& P, const Bases& B, const Launch& L, int
         c->evpool.push_back(e);
       }
       cudaEventRecord(c->evpool[ev], st);
-      launch_ops(L.type, ops, L.count, P.d_terms, B, md, st);
+      launch_ops(L.type, ops, L.count, P.d_terms, P.chains(), B, md, st);
       cudaEventRecord(c->evpool[ev + 1], st);
       c->pending.push_back(hlc_ctx::Pending{L.type, ev});
       return;
     }
     if (!g_prof.on) {
-      launch_ops(L.type, ops, L.count, P.d_terms, B, md, st);
+      launch_ops(L.type, ops, L.count, P.d_terms, P.chains(), B, md, st);
       return;
     }
     cudaStreamSynchronize(st);
     const auto t0 = std::chrono::steady_clock::now();
-    launch_ops(L.type, ops, L.count, P.d_terms, B, md, st);
+    launch_ops(L.type, ops, L.count, P.d_terms, P.chains(), B, md, st);
     cudaStreamSynchronize(st);
     const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     g_prof.ms[L.type] += ms;
@@ -492,7 +517,10 @@ int hmat_alloc(hlc_tree* t, int which, hlc_hmat** out) {
   M->t = t;
   M->which = which;
   cudaError_t e = cudaMalloc(&M->arena, std::max<int64_t>(t->T.arena_doubles, 4) * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&M->ranks, std::max<int32_t>(t->T.nslots, 1) * sizeof(int));
+  // a factor's rank array also holds the slots of the factorisation plan's
+  // temporary partial sums (the plan is built before a factor is allocated)
+  const int64_t slots = (int64_t)t->T.nslots + (which == 1 ? t->chol.tmp_slots : 0);
+  if (e == cudaSuccess) e = cudaMalloc(&M->ranks, std::max<int64_t>(slots, 1) * sizeof(int));
   if (e != cudaSuccess) {
     cudaFree(M->arena);
     cudaFree(M->ranks);
@@ -510,7 +538,7 @@ int check_plan(hlc_tree* t, const Plan& P) {
   sz[BUF_C] = t->T.arena_doubles;
   sz[BUF_TMP] = P.tmp_doubles;
   sz[BUF_VEC] = 6 * t->T.n;
-  const std::string err = validate_plan(P, sz);
+  const std::string err = validate_plan(P, sz, (int64_t)t->T.nslots + P.tmp_slots);
   if (!err.empty()) {
     fprintf(stderr, "hlc: plan rejected: %s\n", err.c_str());
     return HLC_ERR_STATE;
@@ -531,8 +559,8 @@ int build_plans(hlc_tree* t, bool chol, bool solve) {
     }
     if (solve && !t->solve_ready) {
       const int64_t n = t->T.n;
-      plan_solve(t->T, t->fwd, 0, 0, 1);
-      plan_solve(t->T, t->bwd, 1, 0, 1);
+      plan_solve(t->T, t->fwd, 0, 0, 1, chains_enabled());
+      plan_solve(t->T, t->bwd, 1, 0, 1, chains_enabled());
       plan_matvec(t->T, t->mv, n, 2 * n, 1);
       int st;
       if ((st = check_plan(t, t->fwd)) || (st = check_plan(t, t->bwd)) || (st = check_plan(t, t->mv))) return st;
@@ -555,8 +583,8 @@ int build_plans(hlc_tree* t, bool chol, bool solve) {
 int build_lmv_plans(hlc_tree* t) {
   if (t->lmv_ready) return HLC_OK;
   try {
-    plan_trmv(t->T, t->lmv, 0, 0, 1);
-    plan_trmv(t->T, t->lmvt, 1, 0, 1);
+    plan_trmv(t->T, t->lmv, 0, 0, 1, chains_enabled());
+    plan_trmv(t->T, t->lmvt, 1, 0, 1, chains_enabled());
     int st;
     if ((st = check_plan(t, t->lmv)) || (st = check_plan(t, t->lmvt))) return st;
     if ((st = upload_plan(t->lmv)) || (st = upload_plan(t->lmvt))) return st;
@@ -1104,7 +1132,9 @@ int hlc_cholesky(hlc_ctx* c, const hlc_hmat* C, hlc_hmat** L) {
   CK(cudaSetDevice(c->device));
   *L = nullptr;
   hlc_hmat* M = nullptr;
-  int st = hmat_alloc(C->t, 1, &M);
+  int st = build_plans(C->t, true, false);  // sizes the factor's rank array
+  if (st) return st;
+  st = hmat_alloc(C->t, 1, &M);
   if (st) return st;
   st = do_cholesky(C->t, C, M);
   if (st) {
@@ -1638,8 +1668,8 @@ int hlc_matvec_noalloc(hlc_ctx* c, const hlc_hmat* C, const double* x, double* y
   const int md = (int)std::max<int64_t>(t->T.max_dense_dim, t->T.leaf);
   bool done = false;
   if (c->persistent && !c->profiling && !g_prof.on && persistent_enabled()) {
-    if (launch_waves(t->mv.d_waves, (int)t->mv.waves.size(), t->mv.d_trsm, t->mv.d_gemm, B, c->d_gridbar, md,
-                     t->mv.tuned_per_sm, c->stream) == 0) {
+    if (launch_waves(t->mv.d_waves, (int)t->mv.waves.size(), t->mv.d_trsm, t->mv.d_gemm, t->mv.d_chain,
+                     t->mv.chains(), B, c->d_gridbar, md, t->mv.tuned_per_sm, c->stream) == 0) {
       done = true;
       c->launches += 1;
       c->persistent_launches += 1;

@@ -298,6 +298,10 @@ const int64_t kTruncManyRows = 512;   // ... a target with m + n above this uses
 const int64_t kGemmSplitRows = 4096;  // row block of a split product
 const int64_t kGemmSplitK = 2048;     // inner block of a split matrix-vector product
 const int64_t kPendingCols = INT64_MAX;  // no size-forced truncation: flush only on use
+const size_t kTreeMinTerms = 9;          // a truncated sum of this many terms or more ...
+const size_t kTreeLeafTerms = 4;         // ... is summed as a tree over groups of this many
+const int64_t kTempKcap = 128;           // rank capacity of a partial sum
+const int64_t kChainRows = 1024;         // largest diagonal block whose solve is one chain
 
 struct Planner {
   HTree& T;
@@ -516,9 +520,7 @@ struct Planner {
       op.alpha = alpha;
       op.beta = first_write_beta(Y);
       op.pad = 0;
-      const int32_t w = place({Pt}, {Y});
-      P.gemm.push_back(op);
-      seq.push_back(Ref{OP_GEMM, (int64_t)P.gemm.size() - 1, w});
+      emit_gemm(op, {Pt}, {Y});
       return;
     }
     // tall products split into independent row blocks (one CTA each)
@@ -539,9 +541,7 @@ struct Planner {
     op.alpha = alpha;
     op.beta = first_write_beta(Y);
     op.pad = 0;
-    const int32_t w = place({A, B}, {Y});
-    P.gemm.push_back(op);
-    seq.push_back(Ref{OP_GEMM, (int64_t)P.gemm.size() - 1, w});
+    emit_gemm(op, {A, B}, {Y});
   }
   // Y += alpha * X (B marked as the identity)
   void axpy(const PV& Y, const PV& X, Dim m, Dim c, double alpha) {
@@ -556,9 +556,7 @@ struct Planner {
     op.alpha = alpha;
     op.beta = first_write_beta(Y);
     op.pad = 0;
-    const int32_t w = place({X}, {Y});
-    P.gemm.push_back(op);
-    seq.push_back(Ref{OP_GEMM, (int64_t)P.gemm.size() - 1, w});
+    emit_gemm(op, {X}, {Y});
   }
   void trsm(const PV& L, const PV& X, int64_t n, int trans, Dim c) {
     if (n <= 0 || c.n <= 0) return;
@@ -568,9 +566,58 @@ struct Planner {
     op.n = (int32_t)n;
     op.trans = trans;
     op.c = c;
+    if (in_chain) {
+      P.ctrsm.push_back(op);
+      P.citems.push_back(ChainItem{OP_TRSM, 0, (int64_t)P.ctrsm.size() - 1});
+      chain_access({L}, {X});
+      return;
+    }
     const int32_t w = place({L}, {X});
     P.trsm.push_back(op);
     seq.push_back(Ref{OP_TRSM, (int64_t)P.trsm.size() - 1, w});
+  }
+
+  // ---- chains: the ops of a small diagonal block's solve run by one CTA ----
+  bool chains = false;    // emit chains (solve plans)
+  bool in_chain = false;  // collecting the ops of a chain
+  int64_t chain_item0 = 0;
+  std::vector<PV> chain_reads, chain_writes;
+
+  void emit_gemm(const OpGemm& op, const std::vector<PV>& reads, const std::vector<PV>& writes) {
+    if (in_chain) {
+      P.cgemm.push_back(op);
+      P.citems.push_back(ChainItem{OP_GEMM, 0, (int64_t)P.cgemm.size() - 1});
+      chain_access(reads, writes);
+      return;
+    }
+    const int32_t w = place(reads, writes);
+    P.gemm.push_back(op);
+    seq.push_back(Ref{OP_GEMM, (int64_t)P.gemm.size() - 1, w});
+  }
+  void chain_access(const std::vector<PV>& reads, const std::vector<PV>& writes) {
+    chain_reads.insert(chain_reads.end(), reads.begin(), reads.end());
+    chain_writes.insert(chain_writes.end(), writes.begin(), writes.end());
+  }
+  void begin_chain() {
+    in_chain = true;
+    chain_item0 = (int64_t)P.citems.size();
+    chain_reads.clear();
+    chain_writes.clear();
+  }
+  // The chain is one op: it waits for every producer of what any of its ops
+  // reads or writes, and everything after it waits for it.  Temporaries
+  // written inside the chain are among its writes, so they live for its
+  // wave.
+  void end_chain() {
+    in_chain = false;
+    const int64_t nit = (int64_t)P.citems.size() - chain_item0;
+    if (nit == 0) return;
+    // reads that the chain itself wrote first are internal: only the writes
+    // need to be placed for those regions, and a region both read and
+    // written orders the same way as written
+    const int32_t w = place(chain_reads, chain_writes);
+    P.chain.push_back(OpChain{chain_item0, (int32_t)nit, 0});
+    seq.push_back(Ref{OP_CHAIN, (int64_t)P.chain.size() - 1, w});
   }
   void potrf(int32_t b) {
     const Block& B = T.blk[b];
@@ -584,16 +631,43 @@ struct Planner {
     seq.push_back(Ref{OP_POTRF, (int64_t)P.potrf.size() - 1, w});
   }
 
-  void trunc(int32_t b, const std::vector<TermP>& terms, int keep) {
+  // The low-rank target of a truncation: a leaf block of the matrix or a
+  // temporary partial sum (views in BUF_TMP, a rank slot after the
+  // matrix's own).
+  struct Target {
+    PV U, V;
+    int64_t m, n;
+    int32_t kcap, slot;
+  };
+  Target block_target(int32_t b) {
     const Block& B = T.blk[b];
+    return Target{whole(objU[b], B.m, B.kcap), whole(objV[b], B.n, B.kcap), B.m, B.n, B.kcap, B.slot};
+  }
+  // Rank slots of temporary partial sums, numbered after the matrix's
+  // nslots (the rank array of a matrix holds nslots + P.tmp_slots words).
+  Target temp_target(int64_t m, int64_t n) {
+    const int32_t kc = (int32_t)std::min<int64_t>(kTempKcap, std::min(m, n));
+    const int32_t ou = new_tmp(m, kc), ov = new_tmp(n, kc);
+    const int32_t slot = T.nslots + P.tmp_slots++;
+    return Target{whole(ou, m, kc), whole(ov, n, kc), m, n, kc, slot};
+  }
+  TermP as_term(const Target& t) {
+    return TermP{PV{t.U.obj, 0, 0, t.m, t.kcap, false, NOSLOT, t.slot},
+                 PV{t.V.obj, 0, 0, t.n, t.kcap, false, NOSLOT, t.slot}, t.m, t.n, 0, 0, dim(t.kcap, t.slot), 0,
+                 1.0};
+  }
+
+  // One truncation op: target := trunc(target (keep) + sum of the terms),
+  // the terms taken in batches of at most 64 new columns by the kernel.
+  void trunc_op(const Target& tg, const std::vector<TermP>& terms, int keep) {
     OpTrunc op;
-    PV U = whole(objU[b], B.m, B.kcap), V = whole(objV[b], B.n, B.kcap);
+    PV U = tg.U, V = tg.V;
     op.U = mv(U);
     op.V = mv(V);
-    op.m = (int32_t)B.m;
-    op.n = (int32_t)B.n;
-    op.kcap = B.kcap;
-    op.slot = B.slot;
+    op.m = (int32_t)tg.m;
+    op.n = (int32_t)tg.n;
+    op.kcap = tg.kcap;
+    op.slot = tg.slot;
     op.nterms = (int32_t)terms.size();
     op.keep = keep;
     op.term0 = (int64_t)P.terms.size();
@@ -617,14 +691,53 @@ struct Planner {
     }
     const int32_t w = place(reads, {U, V});
     P.trunc.push_back(op);
-    // large targets run on a thread-block cluster
     // a cluster of CTAs streams the rows of large targets, and of mid-size
     // targets that take many terms (several sequential batches of columns)
     int64_t tcols = 0;
     for (const TermP& t : terms) tcols += (t.flags & 1) ? t.urows : (t.flags & 2) ? t.vrows : t.k.n;
-    const bool many = tcols > kTruncManyCols && B.m + B.n > kTruncManyRows;
-    const int32_t ty = (B.m + B.n > kTruncBigRows || many) ? OP_TRUNC_BIG : OP_TRUNC;
+    const bool many = tcols > kTruncManyCols && tg.m + tg.n > kTruncManyRows;
+    const int32_t ty = (tg.m + tg.n > kTruncBigRows || many) ? OP_TRUNC_BIG : OP_TRUNC;
     seq.push_back(Ref{ty, (int64_t)P.trunc.size() - 1, w});
+  }
+
+  // Truncated sum of many terms (Table 1's truncated addition over a sum
+  // whose order the paper leaves open): fewer than kTreeMinTerms terms go
+  // into one op in order; more are summed as a balanced tree -- groups of
+  // kTreeLeafTerms terms truncated on their own into temporaries, adjacent
+  // partial sums combined pairwise (an odd last one moves up) until two
+  // remain, then target := trunc(target + S_1 + S_2).  The ops of a tree
+  // level are independent, so the depth is logarithmic in the number of
+  // terms instead of linear in their columns.
+  void trunc(int32_t b, const std::vector<TermP>& terms, int keep) {
+    const Target tg = block_target(b);
+    if (terms.size() < kTreeMinTerms) {
+      trunc_op(tg, terms, keep);
+      return;
+    }
+    std::vector<Target> level;
+    for (size_t g = 0; g < terms.size(); g += kTreeLeafTerms) {
+      const size_t e = std::min(terms.size(), g + kTreeLeafTerms);
+      const std::vector<TermP> grp(terms.begin() + g, terms.begin() + e);
+      const Target s = temp_target(tg.m, tg.n);
+      trunc_op(s, grp, 0);
+      level.push_back(s);
+    }
+    while (level.size() > 2) {
+      std::vector<Target> next;
+      for (size_t i = 0; i < level.size(); i += 2) {
+        if (i + 1 == level.size()) {
+          next.push_back(level[i]);
+          break;
+        }
+        const Target s = temp_target(tg.m, tg.n);
+        trunc_op(s, {as_term(level[i]), as_term(level[i + 1])}, 0);
+        next.push_back(s);
+      }
+      level.swap(next);
+    }
+    std::vector<TermP> last;
+    for (const Target& s : level) last.push_back(as_term(s));
+    trunc_op(tg, last, keep);
   }
 
   static int64_t term_cap(const TermP& t) {
@@ -720,9 +833,23 @@ struct Planner {
     return T.cl[t.child[0]].hi - t.lo;
   }
 
+  // A subdivided diagonal block of at most kChainRows rows starts a chain
+  // (when chains are on and none is open): its whole solve or product
+  // becomes one op.
+  bool chain_here(int32_t l) const {
+    const Block& L = blk(l);
+    return chains && !in_chain && L.type == BT_SUB && L.m <= kChainRows;
+  }
+
   // X := L^-1 X
   void trsv(int32_t l, const PV& X) {
     const Block& L = blk(l);
+    if (chain_here(l)) {
+      begin_chain();
+      trsv(l, X);
+      end_chain();
+      return;
+    }
     if (L.type == BT_DENSE) {
       trsm(D(l), X, L.m, 0, dim(X.cols, X.dcol));
       return;
@@ -737,6 +864,12 @@ struct Planner {
   // X := L^-T X
   void trsv_t(int32_t l, const PV& X) {
     const Block& L = blk(l);
+    if (chain_here(l)) {
+      begin_chain();
+      trsv_t(l, X);
+      end_chain();
+      return;
+    }
     if (L.type == BT_DENSE) {
       trsm(D(l), X, L.m, 1, dim(X.cols, X.dcol));
       return;
@@ -752,6 +885,12 @@ struct Planner {
   // X1 := L22 X1 + L21 X0 (X0 still unchanged), then X0 := L11 X0
   void trmv(int32_t l, const PV& X) {
     const Block& L = blk(l);
+    if (chain_here(l)) {
+      begin_chain();
+      trmv(l, X);
+      end_chain();
+      return;
+    }
     if (L.type == BT_DENSE) {
       trsm(D(l), X, L.m, 2, dim(X.cols, X.dcol));
       return;
@@ -767,6 +906,12 @@ struct Planner {
   // X1 := L22^T X1
   void trmv_t(int32_t l, const PV& X) {
     const Block& L = blk(l);
+    if (chain_here(l)) {
+      begin_chain();
+      trmv_t(l, X);
+      end_chain();
+      return;
+    }
     if (L.type == BT_DENSE) {
       trsm(D(l), X, L.m, 3, dim(X.cols, X.dcol));
       return;
@@ -1072,6 +1217,15 @@ struct Planner {
       if (!(t.flags & 1)) patch(t.U);
       if (!(t.flags & 2)) patch(t.V);
     }
+    for (OpGemm& g : P.cgemm) {
+      patch(g.Y);
+      patch(g.A);
+      if (g.B.buf >= 0) patch(g.B);
+    }
+    for (OpTrsm& t : P.ctrsm) {
+      patch(t.L);
+      patch(t.X);
+    }
   }
 
   void finish() {
@@ -1088,6 +1242,7 @@ struct Planner {
     std::vector<OpTrsm> t;
     std::vector<OpPotrf> p;
     std::vector<OpTrunc> u;
+    std::vector<OpChain> ch;
     P.launches.clear();
     P.max_trunc_per_wave = 0;
     for (size_t i = 0; i < order.size(); ++i) {
@@ -1097,6 +1252,7 @@ struct Planner {
         case OP_GEMM: pos = (int64_t)g.size(); g.push_back(P.gemm[r.idx]); break;
         case OP_TRSM: pos = (int64_t)t.size(); t.push_back(P.trsm[r.idx]); break;
         case OP_POTRF: pos = (int64_t)p.size(); p.push_back(P.potrf[r.idx]); break;
+        case OP_CHAIN: pos = (int64_t)ch.size(); ch.push_back(P.chain[r.idx]); break;
         default: pos = (int64_t)u.size(); u.push_back(P.trunc[r.idx]); break;  // OP_TRUNC, OP_TRUNC_BIG
       }
       if (!P.launches.empty() && P.launches.back().wave == r.wave && P.launches.back().type == r.type) {
@@ -1110,6 +1266,7 @@ struct Planner {
     P.trsm.swap(t);
     P.potrf.swap(p);
     P.trunc.swap(u);
+    P.chain.swap(ch);
   }
 };
 
@@ -1126,9 +1283,10 @@ void plan_cholesky(HTree& T, Plan& P, bool accumulate) {
 
 // Forward (trans = 0) or backward (trans = 1) solve of the factor against
 // the vector(s) in BUF_VEC at offset voff (n x ncols, ld n).
-void plan_solve(HTree& T, Plan& P, int trans, int64_t voff, int64_t ncols) {
+void plan_solve(HTree& T, Plan& P, int trans, int64_t voff, int64_t ncols, bool chains) {
   P = Plan();
   Planner pl(T, P, BUF_L);
+  pl.chains = chains;
   const int32_t v = pl.add_obj(BUF_VEC, voff, T.n);
   PV X = pl.whole(v, T.n, ncols);
   if (trans)
@@ -1140,9 +1298,10 @@ void plan_solve(HTree& T, Plan& P, int trans, int64_t voff, int64_t ncols) {
 
 // In-place product of the lower factor (trans = 0: X := L X) or of its
 // transpose (trans = 1: X := L^T X) with the vector(s) in BUF_VEC at voff.
-void plan_trmv(HTree& T, Plan& P, int trans, int64_t voff, int64_t ncols) {
+void plan_trmv(HTree& T, Plan& P, int trans, int64_t voff, int64_t ncols, bool chains) {
   P = Plan();
   Planner pl(T, P, BUF_L);
+  pl.chains = chains;
   const int32_t v = pl.add_obj(BUF_VEC, voff, T.n);
   PV X = pl.whole(v, T.n, ncols);
   if (trans)
@@ -1174,8 +1333,9 @@ void plan_recompress(HTree& T, Plan& P) {
 // Every view of every op must stay inside its buffer at full capacity
 // (static extents, ranks at their caps).  Returns an empty string or the
 // first violation.
-std::string validate_plan(const Plan& P, const int64_t* bufsize) {
+std::string validate_plan(const Plan& P, const int64_t* bufsize, int64_t nslots) {
   char msg[256];
+  auto slot_ok = [&](const Dim& d) { return d.slot < (int32_t)nslots; };
   auto check = [&](const Mv& v, int64_t rows, int64_t cols, const char* what, int64_t i) -> bool {
     if (rows <= 0 || cols <= 0) return true;
     if (v.buf < 0 || v.buf >= NBUF || v.off < 0 || v.rs < 0 || v.cs < 0) {
@@ -1193,6 +1353,7 @@ std::string validate_plan(const Plan& P, const int64_t* bufsize) {
   };
   for (size_t i = 0; i < P.gemm.size(); ++i) {
     const OpGemm& g = P.gemm[i];
+    if (!slot_ok(g.m) || !slot_ok(g.k) || !slot_ok(g.c)) return "gemm: rank slot out of range";
     if (!check(g.Y, g.m.n, g.c.n, "gemm.Y", i)) return msg;
     if (g.B.buf == MV_IDENTITY) {
       if (!check(g.A, g.m.n, g.c.n, "axpy.X", i)) return msg;
@@ -1205,7 +1366,39 @@ std::string validate_plan(const Plan& P, const int64_t* bufsize) {
   for (size_t i = 0; i < P.trsm.size(); ++i) {
     const OpTrsm& t = P.trsm[i];
     if (t.n > 128) return "trsm: block larger than 128";
+    if (!slot_ok(t.c)) return "trsm: rank slot out of range";
     if (!check(t.L, t.n, t.n, "trsm.L", i) || !check(t.X, t.n, t.c.n, "trsm.X", i)) return msg;
+  }
+  for (size_t i = 0; i < P.cgemm.size(); ++i) {
+    const OpGemm& g = P.cgemm[i];
+    if (!slot_ok(g.m) || !slot_ok(g.k) || !slot_ok(g.c)) return "chain gemm: rank slot out of range";
+    if (!check(g.Y, g.m.n, g.c.n, "chain gemm.Y", i)) return msg;
+    if (g.B.buf == MV_IDENTITY) {
+      if (!check(g.A, g.m.n, g.c.n, "chain axpy.X", i)) return msg;
+    } else if (g.B.buf == MV_ONES) {
+      if (!check(g.A, g.m.n, g.k.n, "chain gemm.A", i)) return msg;
+    } else {
+      if (!check(g.A, g.m.n, g.k.n, "chain gemm.A", i) || !check(g.B, g.k.n, g.c.n, "chain gemm.B", i)) return msg;
+    }
+  }
+  for (size_t i = 0; i < P.ctrsm.size(); ++i) {
+    const OpTrsm& t = P.ctrsm[i];
+    if (t.n > 128) return "chain trsm: block larger than 128";
+    if (!slot_ok(t.c)) return "chain trsm: rank slot out of range";
+    if (!check(t.L, t.n, t.n, "chain trsm.L", i) || !check(t.X, t.n, t.c.n, "chain trsm.X", i)) return msg;
+  }
+  for (const OpChain& c : P.chain) {
+    if (c.item0 < 0 || c.nitems <= 0 || c.item0 + c.nitems > (int64_t)P.citems.size()) return "chain: item range";
+    for (int64_t q = c.item0; q < c.item0 + c.nitems; ++q) {
+      const ChainItem& it = P.citems[q];
+      if (it.type == OP_TRSM) {
+        if (it.idx < 0 || it.idx >= (int64_t)P.ctrsm.size()) return "chain: trsm index";
+      } else if (it.type == OP_GEMM) {
+        if (it.idx < 0 || it.idx >= (int64_t)P.cgemm.size()) return "chain: gemm index";
+      } else {
+        return "chain: item type";
+      }
+    }
   }
   for (size_t i = 0; i < P.potrf.size(); ++i) {
     const OpPotrf& t = P.potrf[i];
@@ -1215,6 +1408,7 @@ std::string validate_plan(const Plan& P, const int64_t* bufsize) {
   for (size_t i = 0; i < P.trunc.size(); ++i) {
     const OpTrunc& t = P.trunc[i];
     if (t.kcap > 128) return "trunc: rank capacity above 128";
+    if (t.slot < 0 || t.slot >= nslots) return "trunc: rank slot out of range";
     if (!check(t.U, t.m, t.kcap, "trunc.U", i) || !check(t.V, t.n, t.kcap, "trunc.V", i)) return msg;
     if (t.term0 < 0 || t.term0 + t.nterms > (int64_t)P.terms.size()) return "trunc: term range";
     for (int q = 0; q < t.nterms; ++q) {
@@ -1222,6 +1416,7 @@ std::string validate_plan(const Plan& P, const int64_t* bufsize) {
       if (d.roff < 0 || d.coff < 0 || d.roff + d.urows > t.m || d.coff + d.vrows > t.n) return "term: placement";
       const int64_t k = (d.flags & 1) ? d.urows : (d.flags & 2) ? d.vrows : d.k.n;
       if (k > 128) return "term: more than 128 columns";
+      if (!slot_ok(d.k)) return "term: rank slot out of range";
       if (!(d.flags & 1) && !check(d.U, d.urows, k, "term.U", t.term0 + q)) return msg;
       if (!(d.flags & 2) && !check(d.V, d.vrows, k, "term.V", t.term0 + q)) return msg;
     }

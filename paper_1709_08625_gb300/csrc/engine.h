@@ -37,12 +37,15 @@ void layout(HTree& T, int kmax);
 // accumulate: updates of a low-rank block are truncated together right before
 // the block is next used (accumulated updates) instead of one at a time.
 void plan_cholesky(HTree& T, Plan& P, bool accumulate = false);
-void plan_solve(HTree& T, Plan& P, int trans, int64_t voff, int64_t ncols);
+// chains: the solve of every subdivided diagonal block of at most 1024 rows
+// becomes one op (a chain run by one CTA)
+void plan_solve(HTree& T, Plan& P, int trans, int64_t voff, int64_t ncols, bool chains = true);
 void plan_matvec(HTree& T, Plan& P, int64_t xoff, int64_t yoff, int64_t ncols);
 // X := L X (trans 0) or L^T X (trans 1), in place, L the lower factor
-void plan_trmv(HTree& T, Plan& P, int trans, int64_t voff, int64_t ncols);
+void plan_trmv(HTree& T, Plan& P, int trans, int64_t voff, int64_t ncols, bool chains = true);
 void plan_recompress(HTree& T, Plan& P);
-// Bounds check of every view against the buffer sizes (in doubles).
-std::string validate_plan(const Plan& P, const int64_t* bufsize);
+// Bounds check of every view against the buffer sizes (in doubles) and of
+// every rank slot against the rank array's length.
+std::string validate_plan(const Plan& P, const int64_t* bufsize, int64_t nslots);
 
 }  // namespace hlc

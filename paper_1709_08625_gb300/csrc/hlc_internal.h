@@ -104,7 +104,36 @@ struct Bases {
   unsigned long long* phase;  // truncation phase cycle counters, or null
 };
 
-enum OpType : int32_t { OP_POTRF = 0, OP_TRSM = 1, OP_GEMM = 2, OP_TRUNC = 3, OP_TRUNC_BIG = 4, NOPTYPES = 5 };
+enum OpType : int32_t {
+  OP_POTRF = 0,
+  OP_TRSM = 1,
+  OP_GEMM = 2,
+  OP_TRUNC = 3,
+  OP_TRUNC_BIG = 4,
+  OP_CHAIN = 5,
+  NOPTYPES = 6
+};
+
+// A chain: the TRSM and GEMM ops of one small diagonal block's triangular
+// solve (or product with the factor), run in order by one CTA with a block
+// barrier between consecutive ops, instead of one wave each.  Items index
+// the plan's chain arrays (ctrsm for OP_TRSM, cgemm for OP_GEMM).
+struct ChainItem {
+  int32_t type;
+  int32_t pad;
+  int64_t idx;
+};
+struct OpChain {
+  int64_t item0;
+  int32_t nitems;
+  int32_t pad;
+};
+// Device tables of a plan's chains.
+struct ChainTab {
+  const ChainItem* items;
+  const OpTrsm* trsm;
+  const OpGemm* gemm;
+};
 
 // Device error codes recorded in status[0].
 enum DevErr : int32_t { DEV_OK = 0, DEV_NOT_SPD = 1, DEV_RANK = 2, DEV_BAD = 3, DEV_TIMEOUT = 4 };
@@ -162,10 +191,12 @@ struct GridBar {
   unsigned int count, gen, abort, pad;
 };
 
-// TRSM and GEMM op ranges of one wave (persistent execution of a plan).
+// TRSM, GEMM and chain op ranges of one wave (persistent execution of a
+// plan).
 struct WaveRange {
   int64_t trsm0, ntrsm;
   int64_t gemm0, ngemm;
+  int64_t chain0, nchain;
 };
 
 struct Plan {
@@ -174,8 +205,13 @@ struct Plan {
   std::vector<OpPotrf> potrf;
   std::vector<OpTrunc> trunc;
   std::vector<TermD> terms;
+  std::vector<OpChain> chain;
+  std::vector<ChainItem> citems;
+  std::vector<OpTrsm> ctrsm;
+  std::vector<OpGemm> cgemm;
   std::vector<Launch> launches;
   int64_t tmp_doubles = 0;
+  int32_t tmp_slots = 0;  // rank slots of temporary partial sums (after the matrix's)
   int32_t nwaves = 0;
   int64_t max_trunc_per_wave = 0;
   bool checked = false;
@@ -199,8 +235,13 @@ struct Plan {
   OpPotrf* d_potrf = nullptr;
   OpTrunc* d_trunc = nullptr;
   TermD* d_terms = nullptr;
+  OpChain* d_chain = nullptr;
+  ChainItem* d_citems = nullptr;
+  OpTrsm* d_ctrsm = nullptr;
+  OpGemm* d_cgemm = nullptr;
+  ChainTab chains() const { return ChainTab{d_citems, d_ctrsm, d_cgemm}; }
   int64_t nops() const {
-    return (int64_t)gemm.size() + trsm.size() + potrf.size() + trunc.size();
+    return (int64_t)gemm.size() + trsm.size() + potrf.size() + trunc.size() + ctrsm.size() + cgemm.size();
   }
 };
 

@@ -7,6 +7,8 @@
 //                 FP32 in the mixed modes)
 //   k_gemm        strided multiply-add of dense views (H-arithmetic, Table 1),
 //                 with a matrix-vector path for one column
+//   k_chain       chains: the ops of a small diagonal block's solve in order,
+//                 by one CTA
 //   k_waves       a whole triangular solve or matvec as one cooperative launch
 //                 (waves separated by a bounded grid barrier)
 //   reductions    log det = 2 sum log L_ii, dot products (fixed order)
@@ -516,6 +518,27 @@ __global__ void __launch_bounds__(256) k_gemm(const OpGemm* ops, int64_t count, 
   for (int64_t o = blockIdx.x; o < count; o += gridDim.x) do_gemm<T>(ops[o], B, sm);
 }
 
+// A chain: its TRSM and GEMM ops in order, by the whole CTA, a block barrier
+// after each (the next op may read what this one wrote).
+template <class T>
+__device__ void do_chain(const OpChain& c, const ChainTab& ct, const Bases& B, T* sL, GemmSmem<T>& gs) {
+  for (int32_t q = 0; q < c.nitems; ++q) {
+    const ChainItem it = ct.items[c.item0 + q];
+    if (it.type == OP_TRSM)
+      do_trsm<T>(ct.trsm[it.idx], B, sL);
+    else
+      do_gemm<T>(ct.gemm[it.idx], B, gs);
+    __syncthreads();
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_chain(const OpChain* ops, int64_t count, ChainTab ct, Bases B) {
+  extern __shared__ double smd[];
+  __shared__ GemmSmem<T> gs;
+  for (int64_t o = blockIdx.x; o < count; o += gridDim.x) do_chain<T>(ops[o], ct, B, reinterpret_cast<T*>(smd), gs);
+}
+
 // Grid-wide barrier of the persistent kernel.  Thread 0 of each CTA arrives
 // on a counter; the last CTA to arrive resets it and advances the generation
 // the others wait on.  The wait is bounded: after kBarrierNs, or once another
@@ -571,24 +594,33 @@ __device__ bool grid_barrier(GridBar* gb, int* status, unsigned int expected) {
 // within a wave the CTAs take the ops round-robin, and a grid barrier
 // separates consecutive waves.
 __global__ void __launch_bounds__(256) k_waves(const WaveRange* waves, int nwaves, const OpTrsm* trsm,
-                                               const OpGemm* gemm, Bases B, GridBar* gb) {
+                                               const OpGemm* gemm, const OpChain* chain, ChainTab ct, Bases B,
+                                               GridBar* gb) {
   extern __shared__ double sL[];
   __shared__ GemmSmem<double> gd;
   __shared__ GemmSmem<float> gf;
   for (int w = 0; w < nwaves; ++w) {
     const WaveRange wr = waves[w];
-    const int64_t tot = wr.ntrsm + wr.ngemm;
+    const int64_t tot = wr.ntrsm + wr.ngemm + wr.nchain;
     for (int64_t o = blockIdx.x; o < tot; o += gridDim.x) {
       if (o < wr.ntrsm) {
         if (B.mixed)
           do_trsm<float>(trsm[wr.trsm0 + o], B, reinterpret_cast<float*>(sL));
         else
           do_trsm<double>(trsm[wr.trsm0 + o], B, sL);
-      } else if (B.mixed) {
-        do_gemm<float>(gemm[wr.gemm0 + (o - wr.ntrsm)], B, gf);
+      } else if (o < wr.ntrsm + wr.ngemm) {
+        if (B.mixed)
+          do_gemm<float>(gemm[wr.gemm0 + (o - wr.ntrsm)], B, gf);
+        else
+          do_gemm<double>(gemm[wr.gemm0 + (o - wr.ntrsm)], B, gd);
       } else {
-        do_gemm<double>(gemm[wr.gemm0 + (o - wr.ntrsm)], B, gd);
+        const OpChain& c = chain[wr.chain0 + (o - wr.ntrsm - wr.ngemm)];
+        if (B.mixed)
+          do_chain<float>(c, ct, B, reinterpret_cast<float*>(sL), gf);
+        else
+          do_chain<double>(c, ct, B, sL, gd);
       }
+      __syncthreads();
     }
     if (w + 1 < nwaves && !grid_barrier(gb, B.status, gridDim.x)) return;
   }
@@ -615,8 +647,8 @@ int waves_max_per_sm(int max_dense) {
   return per;
 }
 
-int launch_waves(const WaveRange* waves, int nwaves, const OpTrsm* trsm, const OpGemm* gemm, const Bases& B,
-                 GridBar* gb, int max_dense, int per_sm, cudaStream_t st) {
+int launch_waves(const WaveRange* waves, int nwaves, const OpTrsm* trsm, const OpGemm* gemm, const OpChain* chain,
+                 const ChainTab& ct, const Bases& B, GridBar* gb, int max_dense, int per_sm, cudaStream_t st) {
   const int maxper = waves_max_per_sm(max_dense);
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -625,7 +657,8 @@ int launch_waves(const WaveRange* waves, int nwaves, const OpTrsm* trsm, const O
   const int grid = per * sms;
   if (grid <= 0 || nwaves <= 0 || !gb) return -1;
   if (cudaMemsetAsync(gb, 0, sizeof(GridBar), st) != cudaSuccess) return -1;
-  void* args[] = {(void*)&waves, (void*)&nwaves, (void*)&trsm, (void*)&gemm, (void*)&B, (void*)&gb};
+  void* args[] = {(void*)&waves, (void*)&nwaves, (void*)&trsm, (void*)&gemm, (void*)&chain, (void*)&ct, (void*)&B,
+                  (void*)&gb};
   return cudaLaunchCooperativeKernel((void*)k_waves, grid, 256, args, trsm_smem(max_dense),
                                      st) == cudaSuccess
              ? 0
@@ -751,10 +784,17 @@ void launch_aca(const LrAsm* d, int64_t count, double* arena, const double* px, 
 }
 
 
-void launch_ops(int type, const void* ops, int64_t count, const TermD* terms, const Bases& B, int max_dense,
-                cudaStream_t st) {
+void launch_ops(int type, const void* ops, int64_t count, const TermD* terms, const ChainTab& ct, const Bases& B,
+                int max_dense, cudaStream_t st) {
   if (count <= 0) return;
   switch (type) {
+    case OP_CHAIN:
+      if (B.mixed)
+        k_chain<float><<<grid_for(count, 152 * 8), 256, trsm_smem(max_dense), st>>>((const OpChain*)ops, count, ct, B);
+      else
+        k_chain<double><<<grid_for(count, 152 * 8), 256, trsm_smem(max_dense), st>>>((const OpChain*)ops, count, ct,
+                                                                                      B);
+      break;
     case OP_POTRF:
       k_potrf<<<grid_for(count, 152 * 8), 128, (size_t)max_dense * max_dense * sizeof(double), st>>>(
           (const OpPotrf*)ops, count, B);
@@ -812,6 +852,8 @@ int configure_kernels(int max_dense) {
   cudaError_t e2 = cudaFuncSetAttribute(k_trsm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, tneed);
   if (e2 == cudaSuccess) e2 = cudaFuncSetAttribute(k_trsm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, tneed);
   cudaError_t e4 = cudaFuncSetAttribute(k_waves, cudaFuncAttributeMaxDynamicSharedMemorySize, tneed);
+  if (e4 == cudaSuccess) e4 = cudaFuncSetAttribute(k_chain<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, tneed);
+  if (e4 == cudaSuccess) e4 = cudaFuncSetAttribute(k_chain<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, tneed);
   const int e3 = configure_trunc();
   return (e1 == cudaSuccess && e2 == cudaSuccess && e3 == 0 && e4 == cudaSuccess) ? 0 : -1;
 }

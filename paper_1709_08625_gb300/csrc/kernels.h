@@ -19,13 +19,13 @@ void launch_dense_asm(const DenseAsm* d, int64_t count, double* arena, const dou
 // the stopping test holds (and is not full rank) records DEV_RANK in status.
 void launch_aca(const LrAsm* d, int64_t count, double* arena, const double* px, const double* py,
                 const MaternDev& mp, double eps, int* ranks, int* status, cudaStream_t st);
-void launch_ops(int type, const void* ops, int64_t count, const TermD* terms, const Bases& B, int max_dense,
-                cudaStream_t st);
-// One cooperative launch executing all waves of a TRSM/GEMM plan with
+void launch_ops(int type, const void* ops, int64_t count, const TermD* terms, const ChainTab& ct, const Bases& B,
+                int max_dense, cudaStream_t st);
+// One cooperative launch executing all waves of a TRSM/GEMM/chain plan with
 // per_sm CTAs per SM (0 or more than fit: as many as fit); -1 when the
 // cooperative launch is unavailable (the caller then launches wave by wave).
-int launch_waves(const WaveRange* waves, int nwaves, const OpTrsm* trsm, const OpGemm* gemm, const Bases& B,
-                 GridBar* gb, int max_dense, int per_sm, cudaStream_t st);
+int launch_waves(const WaveRange* waves, int nwaves, const OpTrsm* trsm, const OpGemm* gemm, const OpChain* chain,
+                 const ChainTab& ct, const Bases& B, GridBar* gb, int max_dense, int per_sm, cudaStream_t st);
 int waves_max_per_sm(int max_dense);
 // Two CTAs wait at a grid barrier that expects one arrival more than the
 // grid has; the wait ends by its time limit with DEV_TIMEOUT in *status.

@@ -257,7 +257,7 @@ class Context:
     def set_profiling(self, on=True):
         _check(hlc_ctx_set_profiling(self.h, int(bool(on))), "hlc_ctx_set_profiling")
 
-    OPS = ("potrf", "trsm", "gemm", "trunc", "trunc_cluster")
+    OPS = ("potrf", "trsm", "gemm", "trunc", "trunc_cluster", "chain")
 
     # ---- serving -------------------------------------------------------
     def serve_start(self, hbm_budget_bytes, max_slots):
@@ -285,12 +285,12 @@ class Context:
         _check(hlc_serve_stop(self.h), "hlc_serve_stop")
 
     def counters(self, reset=False):
-        a = np.zeros(17)
+        a = np.zeros(20)
         _check(hlc_ctx_counters(self.h, int(bool(reset)), _ptr(a)), "hlc_ctx_counters")
         out = {"launches": int(a[0])}
         for i, name in enumerate(self.OPS):
             out[name] = {"launches": int(a[1 + 3 * i]), "ms": float(a[2 + 3 * i]), "flops": float(a[3 + 3 * i])}
-        out["persistent"] = int(a[16])
+        out["persistent"] = int(a[19])
         return out
 
 

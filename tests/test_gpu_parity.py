@@ -229,7 +229,8 @@ def test_n65536_vs_h_oracle_fp64_and_mixed(hlc, nu):
     # the GPU in HLC_FP64 and in HLC_MIXED against one CPU H-oracle
     # evaluation, element-wise on log det and the quadratic form.  Bars per
     # location: 1e-7 in FP64 (the same H-arithmetic; truncation decisions at
-    # the eps threshold may round differently), 1e-6 in mixed.
+    # the eps threshold may round differently), 1e-6 in mixed.  The nu = 3/2
+    # factor needs more than 64 columns in some blocks: rank capacity 128.
     name = f"n65536_nu{nu}_eps1e-6"
     w = inputs.WORKLOADS[name]
     xy = inputs.workload_points(name)
@@ -239,7 +240,7 @@ def test_n65536_vs_h_oracle_fp64_and_mixed(hlc, nu):
     ho = oracle.h_loglik(xy, z, *th, w["eps"], leaf=w["leaf"], eta=w["eta"])
     c = hlc.Context(0)
     for prec, bar in ((hlc.HLC_FP64, 1e-7), (hlc.HLC_MIXED, 1e-6)):
-        t = c.build_tree(xy, leaf=w["leaf"], eta=w["eta"], eps=w["eps"], precision=prec)
+        t = c.build_tree(xy, leaf=w["leaf"], eta=w["eta"], eps=w["eps"], precision=prec, kmax=128)
         r = t.loglik(hlc.theta(*th), z)
         for k in ("loglik", "logdet", "quad"):
             assert abs(r[k] - ho[k]) / n <= bar, (prec, k, r[k], ho[k])
@@ -331,6 +332,43 @@ def test_persistent_solves_match_wave_launches(hlc):
     # take the ops does not change a single bit
     for key in ("loglik", "logdet", "quad", "quad_factor", "refine_iters"):
         assert on[key] == off[key], key
+
+
+_CHAIN_CASE = """
+import json, sys
+import numpy as np
+sys.path.insert(0, {root!r})
+from paper_1709_08625_gb300 import hlc, inputs
+c = hlc.Context(0)
+out = {{}}
+for prec in (hlc.HLC_FP64, hlc.HLC_MIXED):
+    t = c.build_tree(inputs.points(20000, 1510), leaf=64, eps=1e-6, kmax=128, precision=prec)
+    r = t.loglik(hlc.theta(1.0, 0.05, 0.5, 1e-4), inputs.normal(20000, 1511))
+    out[str(prec)] = {{k: r[k] for k in ("loglik", "logdet", "quad", "quad_factor", "refine_iters")}}
+    z = t.sample(hlc.theta(1.0, 0.05, 0.5, 1e-4), inputs.normal(20000, 1512))
+    out[str(prec)]["sample"] = float(np.sum(z * np.arange(20000)))
+print(json.dumps(out))
+"""
+
+
+def test_chains_match_op_by_op_solves(hlc):
+    # the solves and factor products planned as chains (the ops of each small
+    # diagonal block run in order by one CTA) give the same bits as the same
+    # ops placed one per wave step
+    import json
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    runs = {}
+    for flag in ("1", "0"):
+        env = dict(os.environ, HLC_CHAINS=flag)
+        out = subprocess.run([sys.executable, "-c", _CHAIN_CASE.format(root=root)], env=env, capture_output=True,
+                             text=True, timeout=600)
+        assert out.returncode == 0, out.stderr[-2000:]
+        runs[flag] = json.loads(out.stdout.strip().splitlines()[-1])
+    assert runs["1"] == runs["0"]
 
 
 # --------------------------------------------------------------------------
