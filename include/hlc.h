@@ -44,7 +44,6 @@
  *   HLC_CHAINS=0      plan the solves of small diagonal blocks op by op
  *                     instead of as chains run by one CTA each (same result,
  *                     bit for bit)
- *   HLC_HOST_TREE=1   build the cluster and block trees on the host
  *   HLC_PROFILE=1     time every op launch (synchronising) and print a summary
  *                     at exit
  *   HLC_PHASES=1      count clock cycles per phase of the truncation kernel and
@@ -93,14 +92,28 @@ typedef struct {
   double nugget; /* tau^2 >= 0, added to the diagonal */
 } hlc_theta;
 
+/* ---- block structure variants (Sec. 2.2, App. A) -------------------------- */
+#define HLC_ADM_STANDARD 0  /* admissible iff dist > 0 and min(diam) <= eta dist (App. A) */
+#define HLC_ADM_MAXDIAM 1   /* admissible iff dist > 0 and max(diam) <= eta dist (App. A) */
+#define HLC_ADM_WEAK 2      /* every block of two distinct clusters is admissible */
+#define HLC_SPLIT_GEOMETRIC 0   /* bisect the longest bounding-box axis at its midpoint */
+#define HLC_SPLIT_CARDINALITY 1 /* split the points at the median of the longest axis:
+                                   two equal-sized sub-sets (Sec. 2.2) */
+
 typedef struct {
   int leaf;           /* n_min: largest leaf cluster (Sec. 2.2), 1..128 */
-  double eta;         /* standard admissibility parameter (App. A), > 0 */
+  double eta;         /* admissibility parameter (App. A), > 0 */
   double eps;         /* block accuracy of C~ and of the H-arithmetic (Sec. 2.2) */
   int precision;      /* HLC_FP64, HLC_MIXED or HLC_MIXED_SVD64 */
   double refine_tol;  /* stop the solve when |z - C~ x| <= refine_tol |z| */
   int refine_maxit;   /* at most this many preconditioned CG iterations */
   int kmax;           /* rank capacity of a low-rank block, 1..128 */
+  int admissibility;  /* HLC_ADM_STANDARD (default), HLC_ADM_MAXDIAM or HLC_ADM_WEAK */
+  int split;          /* HLC_SPLIT_GEOMETRIC (default) or HLC_SPLIT_CARDINALITY */
+  int fixed_rank;     /* 0: adaptive rank (accuracy eps); k > 0: fixed-rank mode
+                         (Tables 2 and 3): every low-rank block -- ACA and every
+                         truncation -- keeps at most k columns (those with
+                         sigma_i > eps sigma_1), without an error; k <= kmax */
 } hlc_params;
 
 typedef struct {
@@ -126,7 +139,8 @@ typedef struct {
 } hlc_result;
 
 /* Defaults: leaf 64, eta 2, eps 1e-6, HLC_FP64, refine_tol 1e-12,
- * refine_maxit 100, kmax 64. */
+ * refine_maxit 100, kmax 64, standard admissibility, geometric split,
+ * adaptive rank. */
 void hlc_default_params(hlc_params* p);
 
 /* Description of a status code (static string, never NULL). */
@@ -141,10 +155,11 @@ void hlc_destroy(hlc_ctx* ctx);
  * Cluster tree and block-cluster tree of n points (Sec. 2.2, Def. 2.2, App. A).
  * xy: n x 2 row-major FP64 (x0, y0, x1, y1, ...), host or device.
  * The points are Morton-sorted over their bounding box and bisected
- * geometrically (longest axis of the tight bounding box, at its midpoint)
- * down to clusters of at most p->leaf points; block pairs of the lower
- * triangle with min(diam) <= eta * dist are admissible (low-rank), other
- * pairs with a leaf cluster are dense.  Runs on the device.
+ * (p->split: geometrically, the longest axis of the tight bounding box at its
+ * midpoint; or by cardinality, at the median along that axis) down to
+ * clusters of at most p->leaf points; block pairs of the lower triangle that
+ * are admissible under p->admissibility are low-rank, other pairs with a
+ * leaf cluster are dense.  Runs on the device.
  * The parameters are copied into the tree and used by every later call on it.
  */
 int hlc_build_tree(hlc_ctx* ctx, const double* xy, int64_t n, const hlc_params* p,

@@ -54,7 +54,8 @@ def lib():
         L.orc_dense_loglik.restype = ctypes.c_long
         L.orc_dense_chol_apply.argtypes = [_dp, _dp, _dp, ctypes.c_long] + [ctypes.c_double] * 4 + [_dp]
         L.orc_dense_chol_apply.restype = ctypes.c_long
-        L.orc_h_create.argtypes = [_dp, _dp, ctypes.c_long, ctypes.c_int, ctypes.c_double]
+        L.orc_h_create.argtypes = [_dp, _dp, ctypes.c_long, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                   ctypes.c_int]
         L.orc_h_create.restype = ctypes.c_void_p
         L.orc_h_free.argtypes = [ctypes.c_void_p]
         L.orc_h_info.argtypes = [ctypes.c_void_p, _lp]
@@ -79,6 +80,7 @@ def lib():
         L.orc_truncate.argtypes = [_dp, ctypes.c_long, _dp, ctypes.c_long, ctypes.c_long, ctypes.c_double]
         L.orc_truncate.restype = ctypes.c_long
         L.orc_h_set_theta.argtypes = [ctypes.c_void_p] + [ctypes.c_double] * 4
+        L.orc_h_set_fixed_rank.argtypes = [ctypes.c_void_p, ctypes.c_long]
         _lib = L
     return _lib
 
@@ -165,14 +167,20 @@ def truncate(U, V, eps):
 class HOracle:
     """Plain CPU H-matrix path: tree, assembly, H-Cholesky, likelihood."""
 
-    def __init__(self, xy, leaf=32, eta=2.0):
+    def __init__(self, xy, leaf=32, eta=2.0, admissibility=0, split=0, fixed_rank=0):
+        """admissibility: 0 standard min(diam) <= eta dist, 1 max(diam), 2 weak;
+        split: 0 geometric midpoint, 1 cardinality (median); fixed_rank: 0
+        adaptive, k > 0 at most k columns per low-rank block."""
         xy = np.ascontiguousarray(xy, dtype=np.float64)
         self._x = np.ascontiguousarray(xy[:, 0])
         self._y = np.ascontiguousarray(xy[:, 1])
         self.n = self._x.size
-        self.h = lib().orc_h_create(_d(self._x), _d(self._y), self.n, int(leaf), float(eta))
+        self.h = lib().orc_h_create(_d(self._x), _d(self._y), self.n, int(leaf), float(eta), int(admissibility),
+                                    int(split))
         if not self.h:
             raise ValueError("orc_h_create: bad argument")
+        if fixed_rank:
+            lib().orc_h_set_fixed_rank(self.h, int(fixed_rank))
 
     def __del__(self):
         if getattr(self, "h", None):
@@ -273,9 +281,10 @@ class HOracle:
         return Uk, Vk
 
 
-def h_loglik(xy, z, sigma2, ell, nu, nugget, eps, leaf=32, eta=2.0, tol=1e-12, maxit=100, accumulate=False):
+def h_loglik(xy, z, sigma2, ell, nu, nugget, eps, leaf=32, eta=2.0, tol=1e-12, maxit=100, accumulate=False,
+             admissibility=0, split=0, fixed_rank=0):
     """One oracle evaluation: tree, assembly, H-Cholesky, eq. (2) + preconditioned CG."""
-    H = HOracle(xy, leaf=leaf, eta=eta)
+    H = HOracle(xy, leaf=leaf, eta=eta, admissibility=admissibility, split=split, fixed_rank=fixed_rank)
     H.assemble(sigma2, ell, nu, nugget, eps)
     H.cholesky(eps, accumulate=accumulate)
     r = H.loglik(z, tol=tol, maxit=maxit)

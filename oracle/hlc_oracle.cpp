@@ -236,9 +236,10 @@ void jacobi_svd(const Mat& B0, Mat& X, std::vector<double>& S, Mat& Y) {
 }
 
 // Truncation of R = U V^T (Remark A.1): QR of both factors, SVD of the
-// small core R_u R_v^T, keep the singular values sigma_i > eps * sigma_1.
+// small core R_u R_v^T, keep the singular values sigma_i > eps * sigma_1 --
+// at most kfix of them in the fixed-rank mode of Tables 2 and 3 (kfix > 0).
 // On return U is m x k, V is n x k with U V^T the truncated matrix.
-void truncate_lr(Mat& U, Mat& V, double eps) {
+void truncate_lr(Mat& U, Mat& V, double eps, long kfix = 0) {
   const long K = U.n;
   if (K == 0) return;
   Mat Qu, Ru, Qv, Rv;
@@ -257,6 +258,7 @@ void truncate_lr(Mat& U, Mat& V, double eps) {
   long k = 0;
   if (!S.empty() && S[0] > 0.0)
     while (k < (long)S.size() && S[k] > eps * S[0]) ++k;
+  if (kfix > 0 && k > kfix) k = kfix;
   Mat Un(U.m, k), Vn(V.m, k);
   for (long c = 0; c < k; ++c) {
     for (long i = 0; i < U.m; ++i) {
@@ -372,6 +374,9 @@ struct HTree {
   int depth = 0;
   Theta th{1, 1, 0.5, 0};
   double eps = 1e-6;
+  long kfix = 0;  // fixed-rank mode (Tables 2 and 3): at most kfix columns per block
+  int adm = 0;    // 0 standard (min diam), 1 max diam, 2 weak
+  int split = 0;  // 0 geometric midpoint, 1 cardinality (median)
   bool assembled = false, factored = false;
 };
 
@@ -398,9 +403,12 @@ uint64_t morton_key(double cx, double cy, const double* lo, const double* hi) {
   return key;
 }
 
-// Recursive geometric bisection: tight bounding box; split the longest axis
-// (x on ties) at its midpoint; coordinates <= midpoint go left, stable in the
-// current order; stop at size <= leaf, or when a side would be empty.
+// Recursive bisection: tight bounding box, its longest axis (x on ties).
+// Geometric rule: coordinates <= the axis midpoint go left.  Cardinality rule
+// (the "two equal sized sub-sets" of Sec. 2.2): the floor(size/2) points with
+// the smallest coordinates go left, ties taken in the current order.  Both
+// keep the current order within each side; stop at size <= leaf, or when a
+// side would be empty.
 int build_cluster(HTree& T, const double* x, const double* y, std::vector<int>& idx,
                   long lo, long hi, int level) {
   Cluster c;
@@ -423,11 +431,22 @@ int build_cluster(HTree& T, const double* x, const double* y, std::vector<int>& 
   if (hi - lo <= T.leaf) return id;
   const double ex = c.bmax[0] - c.bmin[0], ey = c.bmax[1] - c.bmin[1];
   const int axis = (ex >= ey) ? 0 : 1;
-  const double mid = 0.5 * (c.bmin[axis] + c.bmax[axis]);
   std::vector<int> left, right;
-  for (long i = lo; i < hi; ++i) {
-    const double v = axis == 0 ? x[idx[i]] : y[idx[i]];
-    (v <= mid ? left : right).push_back(idx[i]);
+  if (T.split == 0) {
+    const double mid = 0.5 * (c.bmin[axis] + c.bmax[axis]);
+    for (long i = lo; i < hi; ++i) {
+      const double v = axis == 0 ? x[idx[i]] : y[idx[i]];
+      (v <= mid ? left : right).push_back(idx[i]);
+    }
+  } else {
+    // positions of the cluster sorted by coordinate, ties by position
+    std::vector<long> ord(hi - lo);
+    std::iota(ord.begin(), ord.end(), lo);
+    const double* co = axis == 0 ? x : y;
+    std::stable_sort(ord.begin(), ord.end(), [&](long a, long b) { return co[idx[a]] < co[idx[b]]; });
+    std::vector<char> goes_left(hi - lo, 0);
+    for (long q = 0; q < (hi - lo) / 2; ++q) goes_left[ord[q] - lo] = 1;
+    for (long i = lo; i < hi; ++i) (goes_left[i - lo] ? left : right).push_back(idx[i]);
   }
   if (left.empty() || right.empty()) return id;
   long pos = lo;
@@ -455,11 +474,15 @@ double box_dist(const Cluster& a, const Cluster& b) {
   return std::sqrt(d2);
 }
 
-// Standard admissibility (App. A): min(diam) <= eta * dist, with dist > 0.
+// Admissibility (App. A) of two distinct clusters: standard
+// min(diam) <= eta dist, or max(diam) <= eta dist, both with dist > 0; weak
+// admissibility takes every such pair.
 bool admissible(const HTree& T, int r, int s) {
+  if (T.adm == 2) return true;
   const double dist = box_dist(T.cl[r], T.cl[s]);
   if (!(dist > 0.0)) return false;
-  return std::min(box_diam(T.cl[r]), box_diam(T.cl[s])) <= T.eta * dist;
+  const double dr = box_diam(T.cl[r]), ds = box_diam(T.cl[s]);
+  return (T.adm == 1 ? std::max(dr, ds) : std::min(dr, ds)) <= T.eta * dist;
 }
 
 // Block-cluster tree over the lower triangle (row cluster at or after the
@@ -782,7 +805,7 @@ void flush(HCtx& H, int b) {
 // so that every core SVD stays small.  An empty (U, V) starts from zero.
 constexpr long kTruncBatch = 64;
 
-void trunc_sum(Mat& CU, Mat& CV, long m, long n, const std::vector<Term>& terms, double eps) {
+void trunc_sum(Mat& CU, Mat& CV, long m, long n, const std::vector<Term>& terms, double eps, long kfix) {
   size_t t0 = 0;
   while (t0 < terms.size()) {
     size_t t1 = t0;
@@ -803,7 +826,7 @@ void trunc_sum(Mat& CU, Mat& CV, long m, long n, const std::vector<Term>& terms,
         for (long i = 0; i < t.V.m; ++i) V(t.coff + i, col) = t.V(i, l);
       }
     }
-    truncate_lr(U, V, eps);
+    truncate_lr(U, V, eps, kfix);
     CU = std::move(U);
     CV = std::move(V);
     t0 = t1;
@@ -826,7 +849,7 @@ void add_terms(HCtx& H, int c, std::vector<Term>& terms) {
   Block& C = H.b(c);
   const long m = H.rows(c), n = H.cols(c);
   if (terms.size() < kTreeMinTerms) {
-    trunc_sum(C.U, C.V, m, n, terms, H.eps);
+    trunc_sum(C.U, C.V, m, n, terms, H.eps, H.T->kfix);
     return;
   }
   std::vector<Term> level;
@@ -837,7 +860,7 @@ void add_terms(HCtx& H, int c, std::vector<Term>& terms) {
     s.U = Mat(m, 0);
     s.V = Mat(n, 0);
     s.roff = s.coff = 0;
-    trunc_sum(s.U, s.V, m, n, grp, H.eps);
+    trunc_sum(s.U, s.V, m, n, grp, H.eps, H.T->kfix);
     level.push_back(std::move(s));
   }
   while (level.size() > 2) {
@@ -854,12 +877,12 @@ void add_terms(HCtx& H, int c, std::vector<Term>& terms) {
       s.U = Mat(m, 0);
       s.V = Mat(n, 0);
       s.roff = s.coff = 0;
-      trunc_sum(s.U, s.V, m, n, pair, H.eps);
+      trunc_sum(s.U, s.V, m, n, pair, H.eps, H.T->kfix);
       next.push_back(std::move(s));
     }
     level.swap(next);
   }
-  trunc_sum(C.U, C.V, m, n, level, H.eps);
+  trunc_sum(C.U, C.V, m, n, level, H.eps, H.T->kfix);
 }
 
 // C += U V^T (with truncation when C is low-rank).
@@ -1261,12 +1284,14 @@ long orc_dense_chol_apply(const double* x, const double* y, const double* xi, lo
   return 0;
 }
 
-void* orc_h_create(const double* x, const double* y, long n, int leaf, double eta) {
-  if (n <= 0 || leaf < 1 || !(eta > 0.0)) return nullptr;
+void* orc_h_create(const double* x, const double* y, long n, int leaf, double eta, int adm, int split) {
+  if (n <= 0 || leaf < 1 || !(eta > 0.0) || adm < 0 || adm > 2 || split < 0 || split > 1) return nullptr;
   HTree* T = new HTree();
   T->n = n;
   T->leaf = leaf;
   T->eta = eta;
+  T->adm = adm;
+  T->split = split;
   // Morton order over the global bounding box; ties by user index.
   double lo[2] = {INFINITY, INFINITY}, hi[2] = {-INFINITY, -INFINITY};
   for (long i = 0; i < n; ++i) {
@@ -1374,8 +1399,10 @@ int orc_h_assemble(void* h, double sigma2, double ell, double nu, double nugget,
       b.U = Mat();
       b.V = Mat();
     } else {
-      aca(*T, cr.lo, cr.size(), cs.lo, cs.size(), eps, kmax, b.U, b.V);
-      truncate_lr(b.U, b.V, eps);
+      // fixed-rank mode: ACA stops after kfix crosses
+      const long kaca = T->kfix > 0 ? std::min<long>(kmax, T->kfix) : kmax;
+      aca(*T, cr.lo, cr.size(), cs.lo, cs.size(), eps, kaca, b.U, b.V);
+      truncate_lr(b.U, b.V, eps, T->kfix);
     }
   }
   T->assembled = true;
@@ -1629,6 +1656,14 @@ long orc_truncate(double* U, long m, double* V, long n, long K, double eps) {
 }
 
 // Set theta without assembling (for orc_h_aca_block).
+// Fixed-rank mode (Tables 2 and 3): every low-rank block -- ACA and every
+// truncation -- keeps at most k columns; k = 0 restores the adaptive rank.
+int orc_h_set_fixed_rank(void* h, long k) {
+  if (k < 0) return -1;
+  static_cast<HTree*>(h)->kfix = k;
+  return 0;
+}
+
 int orc_h_set_theta(void* h, double sigma2, double ell, double nu, double nugget) {
   HTree* T = static_cast<HTree*>(h);
   T->th = Theta{sigma2, ell, nu, nugget};

@@ -640,8 +640,8 @@ int do_assemble(hlc_tree* t, const hlc_theta* th, hlc_hmat* C) {
   // quadratic form z^T C~^-1 z inherits every perturbation of C~ amplified by
   // its condition number (FP32 ACA panels moved |dL|/n by ~5e-4 at
   // n = 524,288, ell = 0.0864, nugget 1e-4).
-  launch_aca(t->d_lr, (int64_t)t->T.lr_asm.size(), C->arena, t->d_px, t->d_py, mp, t->p.eps, C->ranks,
-             c->d_status, c->stream);
+  launch_aca(t->d_lr, (int64_t)t->T.lr_asm.size(), C->arena, t->d_px, t->d_py, mp, t->p.eps, t->p.fixed_rank,
+             C->ranks, c->d_status, c->stream);
   Bases B = make_bases(t, nullptr, C->arena, C->ranks, false);
   run_plan(t, t->recomp, B, c->stream);
   CK(cudaGetLastError());
@@ -815,6 +815,9 @@ void hlc_default_params(hlc_params* p) {
   p->refine_tol = 1e-12;
   p->refine_maxit = 100;
   p->kmax = 64;
+  p->admissibility = HLC_ADM_STANDARD;
+  p->split = HLC_SPLIT_GEOMETRIC;
+  p->fixed_rank = 0;
 }
 
 const char* hlc_strerror(int s) {
@@ -943,7 +946,10 @@ int hlc_build_tree(hlc_ctx* c, const double* xy, int64_t n, const hlc_params* p,
   else
     hlc_default_params(&q);
   if (q.leaf < 1 || q.leaf > 128 || !(q.eta > 0.0) || !(q.eps > 0.0) || q.kmax < 1 || q.kmax > 128 ||
-      (q.precision != HLC_FP64 && q.precision != HLC_MIXED && q.precision != HLC_MIXED_SVD64) || q.refine_maxit < 0)
+      (q.precision != HLC_FP64 && q.precision != HLC_MIXED && q.precision != HLC_MIXED_SVD64) ||
+      q.refine_maxit < 0 || q.admissibility < HLC_ADM_STANDARD || q.admissibility > HLC_ADM_WEAK ||
+      (q.split != HLC_SPLIT_GEOMETRIC && q.split != HLC_SPLIT_CARDINALITY) || q.fixed_rank < 0 ||
+      q.fixed_rank > q.kmax)
     return HLC_ERR_ARG;
   *out = nullptr;
   CK(cudaSetDevice(c->device));
@@ -953,7 +959,6 @@ int hlc_build_tree(hlc_ctx* c, const double* xy, int64_t n, const hlc_params* p,
   t->p = q;
   // points on the device; the trees are built there (Morton sort, bisection,
   // block-cluster tree) and their structure copied to the host planner
-  const bool host_tree = getenv("HLC_HOST_TREE") && getenv("HLC_HOST_TREE")[0] == '1';
   double* d_xy = nullptr;
   CK(cudaMalloc(&d_xy, 2 * n * sizeof(double)));
   CK(cudaMemcpy(d_xy, xy, 2 * n * sizeof(double), is_device_ptr(xy) ? cudaMemcpyDeviceToDevice
@@ -963,25 +968,16 @@ int hlc_build_tree(hlc_ctx* c, const double* xy, int64_t n, const hlc_params* p,
     t->T.leaf = q.leaf;
     t->T.eta = q.eta;
     t->T.eps = q.eps;
-    if (host_tree) {
-      std::vector<double> hxy((size_t)2 * n), hx(n), hy(n);
-      CK(cudaMemcpy(hxy.data(), d_xy, 2 * n * sizeof(double), cudaMemcpyDeviceToHost));
-      for (int64_t i = 0; i < n; ++i) {
-        hx[i] = hxy[2 * i];
-        hy[i] = hxy[2 * i + 1];
-      }
-      tree_from_points(t->T, hx.data(), hy.data(), n, q.leaf, q.eta);
-      block_tree(t->T);
-    } else {
-      int depth = 0;
-      if (device_tree_build(d_xy, n, q.leaf, q.eta, c->stream, t->T.perm, t->T.cl, t->T.blk, &depth) != 0) {
-        cudaFree(d_xy);
-        return HLC_ERR_CUDA;
-      }
-      t->T.depth = depth;
-      collect_leaf_list(t->T);
+    int depth = 0;
+    if (device_tree_build(d_xy, n, q.leaf, q.eta, q.admissibility, q.split, c->stream, t->T.perm, t->T.cl, t->T.blk,
+                          &depth) != 0) {
+      cudaFree(d_xy);
+      return HLC_ERR_CUDA;
     }
+    t->T.depth = depth;
+    collect_leaf_list(t->T);
     t->T.eps = q.eps;
+    t->T.kfix = q.fixed_rank;
     layout(t->T, q.kmax);
     plan_recompress(t->T, t->recomp);
   } catch (const std::bad_alloc&) {

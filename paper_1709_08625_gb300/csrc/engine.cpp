@@ -26,170 +26,8 @@
 namespace hlc {
 
 // ---------------------------------------------------------------------------
-// Tree construction on the host (used to validate the device tree build and
-// as the structure the planner walks).
+// Leaf list of the block-cluster tree (built on the device, tree.cu).
 // ---------------------------------------------------------------------------
-static uint64_t interleave32(uint32_t qx, uint32_t qy) {
-  uint64_t k = 0;
-  for (int b = 0; b < 32; ++b) {
-    k |= (uint64_t)((qx >> b) & 1u) << (2 * b);
-    k |= (uint64_t)((qy >> b) & 1u) << (2 * b + 1);
-  }
-  return k;
-}
-
-static uint32_t quantise(double c, double lo, double hi) {
-  const double range = hi - lo;
-  if (!(range > 0.0)) return 0u;
-  const double t = (c - lo) / range * 4294967295.0;
-  return (uint32_t)std::floor(t);
-}
-
-void tree_from_points(HTree& T, const double* x, const double* y, int64_t n, int leaf, double eta) {
-  T.n = n;
-  T.leaf = leaf;
-  T.eta = eta;
-  double lo[2] = {INFINITY, INFINITY}, hi[2] = {-INFINITY, -INFINITY};
-  for (int64_t i = 0; i < n; ++i) {
-    lo[0] = std::min(lo[0], x[i]);
-    hi[0] = std::max(hi[0], x[i]);
-    lo[1] = std::min(lo[1], y[i]);
-    hi[1] = std::max(hi[1], y[i]);
-  }
-  std::vector<std::pair<uint64_t, int32_t>> kv(n);
-  for (int64_t i = 0; i < n; ++i)
-    kv[i] = {interleave32(quantise(x[i], lo[0], hi[0]), quantise(y[i], lo[1], hi[1])), (int32_t)i};
-  std::sort(kv.begin(), kv.end());
-  std::vector<int32_t> idx(n);
-  for (int64_t i = 0; i < n; ++i) idx[i] = kv[i].second;
-
-  // level-by-level bisection; children are appended in order, so clusters
-  // are numbered breadth-first with increasing lo inside a level.
-  T.cl.clear();
-  Cluster root{};
-  root.lo = 0;
-  root.hi = n;
-  root.child[0] = root.child[1] = -1;
-  root.level = 0;
-  T.cl.push_back(root);
-  std::vector<int32_t> frontier{0}, next;
-  std::vector<int32_t> tmp;
-  T.depth = 0;
-  while (!frontier.empty()) {
-    next.clear();
-    for (int32_t c : frontier) {
-      Cluster& C = T.cl[c];
-      C.bmin[0] = C.bmin[1] = INFINITY;
-      C.bmax[0] = C.bmax[1] = -INFINITY;
-      for (int64_t i = C.lo; i < C.hi; ++i) {
-        const double px = x[idx[i]], py = y[idx[i]];
-        C.bmin[0] = std::min(C.bmin[0], px);
-        C.bmax[0] = std::max(C.bmax[0], px);
-        C.bmin[1] = std::min(C.bmin[1], py);
-        C.bmax[1] = std::max(C.bmax[1], py);
-      }
-      T.depth = std::max(T.depth, C.level);
-      if (C.size() <= leaf) continue;
-      const double ex = C.bmax[0] - C.bmin[0], ey = C.bmax[1] - C.bmin[1];
-      const int ax = ex >= ey ? 0 : 1;
-      const double mid = 0.5 * (C.bmin[ax] + C.bmax[ax]);
-      const double* co = ax == 0 ? x : y;
-      tmp.clear();
-      int64_t nl = 0;
-      for (int64_t i = C.lo; i < C.hi; ++i)
-        if (co[idx[i]] <= mid) ++nl;
-      if (nl == 0 || nl == C.size()) continue;  // all points coincide on the axis
-      tmp.reserve(C.size());
-      for (int64_t i = C.lo; i < C.hi; ++i)
-        if (co[idx[i]] <= mid) tmp.push_back(idx[i]);
-      for (int64_t i = C.lo; i < C.hi; ++i)
-        if (!(co[idx[i]] <= mid)) tmp.push_back(idx[i]);
-      std::copy(tmp.begin(), tmp.end(), idx.begin() + C.lo);
-      Cluster a{}, b{};
-      a.lo = C.lo;
-      a.hi = C.lo + nl;
-      b.lo = C.lo + nl;
-      b.hi = C.hi;
-      a.level = b.level = C.level + 1;
-      a.child[0] = a.child[1] = b.child[0] = b.child[1] = -1;
-      const int32_t ia = (int32_t)T.cl.size();
-      T.cl.push_back(a);
-      T.cl.push_back(b);
-      T.cl[c].child[0] = ia;
-      T.cl[c].child[1] = ia + 1;
-      next.push_back(ia);
-      next.push_back(ia + 1);
-    }
-    frontier.swap(next);
-  }
-  T.perm = idx;
-  T.px.resize(n);
-  T.py.resize(n);
-  for (int64_t i = 0; i < n; ++i) {
-    T.px[i] = x[idx[i]];
-    T.py[i] = y[idx[i]];
-  }
-}
-
-static double diam(const Cluster& c) {
-  const double ex = c.bmax[0] - c.bmin[0], ey = c.bmax[1] - c.bmin[1];
-  return std::sqrt(ex * ex + ey * ey);
-}
-
-static double dist(const Cluster& a, const Cluster& b) {
-  double d2 = 0.0;
-  for (int d = 0; d < 2; ++d) {
-    const double g = std::max(0.0, std::max(a.bmin[d] - b.bmax[d], b.bmin[d] - a.bmax[d]));
-    d2 += g * g;
-  }
-  return std::sqrt(d2);
-}
-
-bool is_admissible(const HTree& T, int r, int s) {
-  const double d = dist(T.cl[r], T.cl[s]);
-  if (!(d > 0.0)) return false;
-  return std::min(diam(T.cl[r]), diam(T.cl[s])) <= T.eta * d;
-}
-
-static int32_t build_block(HTree& T, int32_t r, int32_t s) {
-  const int32_t id = (int32_t)T.blk.size();
-  Block b{};
-  b.r = r;
-  b.s = s;
-  b.diag = (r == s);
-  for (int q = 0; q < 4; ++q) b.ch[q] = -1;
-  b.m = T.cl[r].size();
-  b.n = T.cl[s].size();
-  b.slot = -1;
-  b.leaf_index = -1;
-  T.blk.push_back(b);
-  const Cluster cr = T.cl[r], cs = T.cl[s];
-  if (r == s) {
-    if (cr.leaf()) {
-      T.blk[id].type = BT_DENSE;
-    } else {
-      T.blk[id].type = BT_SUB;
-      const int32_t a = build_block(T, cr.child[0], cr.child[0]);
-      const int32_t c = build_block(T, cr.child[1], cr.child[0]);
-      const int32_t d = build_block(T, cr.child[1], cr.child[1]);
-      T.blk[id].ch[0] = a;
-      T.blk[id].ch[2] = c;
-      T.blk[id].ch[3] = d;
-    }
-  } else if (is_admissible(T, r, s)) {
-    T.blk[id].type = BT_LR;
-  } else if (cr.leaf() || cs.leaf()) {
-    T.blk[id].type = BT_DENSE;
-  } else {
-    T.blk[id].type = BT_SUB;
-    int32_t kids[4];
-    for (int i = 0; i < 2; ++i)
-      for (int j = 0; j < 2; ++j) kids[2 * i + j] = build_block(T, cr.child[i], cs.child[j]);
-    for (int q = 0; q < 4; ++q) T.blk[id].ch[q] = kids[q];
-  }
-  return id;
-}
-
 static void collect_leaves(HTree& T, int32_t b) {
   Block& B = T.blk[b];
   if (B.type != BT_SUB) {
@@ -199,13 +37,6 @@ static void collect_leaves(HTree& T, int32_t b) {
   }
   for (int q = 0; q < 4; ++q)
     if (T.blk[b].ch[q] >= 0) collect_leaves(T, T.blk[b].ch[q]);
-}
-
-void block_tree(HTree& T) {
-  T.blk.clear();
-  T.leaves.clear();
-  build_block(T, 0, 0);
-  collect_leaves(T, 0);
 }
 
 void collect_leaf_list(HTree& T) {
@@ -672,6 +503,8 @@ struct Planner {
     op.keep = keep;
     op.term0 = (int64_t)P.terms.size();
     op.eps = T.eps;
+    op.kfix = T.kfix;
+    op.pad = 0;
     std::vector<PV> reads;
     for (const TermP& t : terms) {
       TermD d;
@@ -1216,6 +1049,10 @@ struct Planner {
     for (TermD& t : P.terms) {
       if (!(t.flags & 1)) patch(t.U);
       if (!(t.flags & 2)) patch(t.V);
+    }
+    for (OpTrunc& t : P.trunc) {  // targets that are temporary partial sums
+      patch(t.U);
+      patch(t.V);
     }
     for (OpGemm& g : P.cgemm) {
       patch(g.Y);

@@ -11,6 +11,7 @@ struct HTree {
   double eta = 2.0;
   double eps = 1e-6;
   int kmax = 64;
+  int kfix = 0;  // fixed-rank mode: at most kfix columns per low-rank block
   int depth = 0;
   std::vector<double> px, py;   // points in tree order
   std::vector<int32_t> perm;    // tree position -> caller index
@@ -24,12 +25,7 @@ struct HTree {
   std::vector<LrAsm> lr_asm;
 };
 
-// Morton order + breadth-first geometric bisection (host reference build).
-void tree_from_points(HTree& T, const double* x, const double* y, int64_t n, int leaf, double eta);
-bool is_admissible(const HTree& T, int r, int s);
-// Block-cluster tree over the lower triangle, leaves depth-first.
-void block_tree(HTree& T);
-// Leaf list (depth-first) of a block tree built elsewhere (device build).
+// Leaf list (depth-first) of the block tree built on the device.
 void collect_leaf_list(HTree& T);
 // Arena offsets, rank capacities and rank slots of the leaves.
 void layout(HTree& T, int kmax);

@@ -81,7 +81,8 @@ struct TermD {
 };
 
 // Target := trunc(target + sum of terms[term0 .. term0 + nterms)) at block
-// accuracy eps; target U (m x kcap), V (n x kcap), rank in ranks[slot].
+// accuracy eps (and at most kfix columns when kfix > 0); target U (m x kcap),
+// V (n x kcap), rank in ranks[slot].
 // keep = 0 ignores the target's current content (assembly).
 struct OpTrunc {
   Mv U, V;
@@ -90,6 +91,8 @@ struct OpTrunc {
   int32_t nterms, keep;
   int64_t term0;
   double eps;
+  int32_t kfix;  // fixed-rank mode: keep at most kfix columns (0: adaptive)
+  int32_t pad;
 };
 
 // Base pointers handed to every op kernel.

@@ -72,7 +72,7 @@ constexpr int ACA_ROWS = 4 * ACA_KCAP;
 template <class T>
 __global__ void __launch_bounds__(ACA_THREADS) k_aca(const LrAsm* blks, int64_t count, double* arena,
                                                       const double* px, const double* py, MaternDev mp,
-                                                      double eps, int* ranks, int* status) {
+                                                      double eps, int kfix, int* ranks, int* status) {
   __shared__ double s_ui[ACA_KCAP], s_vj[ACA_KCAP];
   __shared__ double s_cu[ACA_THREADS / 32][8], s_cv[ACA_THREADS / 32][8];
   __shared__ int used_r[ACA_ROWS], used_c[ACA_KCAP];
@@ -84,7 +84,10 @@ __global__ void __launch_bounds__(ACA_THREADS) k_aca(const LrAsm* blks, int64_t 
     const int m = b.m, n = b.n;
     // kcap > ACA_KCAP is refused when the tree is laid out; clamp anyway so
     // that no index below can leave the shared arrays
-    const int kcap = b.kcap < ACA_KCAP ? b.kcap : ACA_KCAP;
+    int kcap = b.kcap < ACA_KCAP ? b.kcap : ACA_KCAP;
+    // fixed-rank mode: at most kfix crosses, reaching them is not an error
+    const bool fixed_stop = kfix > 0 && kfix < kcap;
+    if (fixed_stop) kcap = kfix;
     double* U = arena + b.offU;
     double* V = arena + b.offV;
     int k = 0, next = 0, zero_tries = 0, nur = 0, nuc = 0;
@@ -230,7 +233,7 @@ __global__ void __launch_bounds__(ACA_THREADS) k_aca(const LrAsm* blks, int64_t 
     // capacity is the full rank min(m, n), where the approximant is exact.
     if (tid == 0) {
       ranks[b.slot] = k;
-      if (!converged && k < (m < n ? m : n)) record_error(status, DEV_RANK, k);
+      if (!converged && !fixed_stop && k < (m < n ? m : n)) record_error(status, DEV_RANK, k);
     }
     __syncthreads();
   }
@@ -777,9 +780,9 @@ void launch_dense_asm(const DenseAsm* d, int64_t count, double* arena, const dou
   k_dense_asm<<<grid_for(count, 152 * 16), 256, 0, st>>>(d, count, arena, px, py, mp);
 }
 void launch_aca(const LrAsm* d, int64_t count, double* arena, const double* px, const double* py,
-                const MaternDev& mp, double eps, int* ranks, int* status, cudaStream_t st) {
+                const MaternDev& mp, double eps, int kfix, int* ranks, int* status, cudaStream_t st) {
   if (count <= 0) return;
-  k_aca<double><<<grid_for(count, 152 * 8), ACA_THREADS, 0, st>>>(d, count, arena, px, py, mp, eps, ranks,
+  k_aca<double><<<grid_for(count, 152 * 8), ACA_THREADS, 0, st>>>(d, count, arena, px, py, mp, eps, kfix, ranks,
                                                                    status);
 }
 

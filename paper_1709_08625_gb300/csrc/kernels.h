@@ -17,8 +17,9 @@ void launch_dense_asm(const DenseAsm* d, int64_t count, double* arena, const dou
                       const MaternDev& mp, cudaStream_t st);
 // ACA of every admissible leaf; a leaf that reaches its rank capacity before
 // the stopping test holds (and is not full rank) records DEV_RANK in status.
+// kfix > 0 (fixed-rank mode): at most kfix crosses, without an error.
 void launch_aca(const LrAsm* d, int64_t count, double* arena, const double* px, const double* py,
-                const MaternDev& mp, double eps, int* ranks, int* status, cudaStream_t st);
+                const MaternDev& mp, double eps, int kfix, int* ranks, int* status, cudaStream_t st);
 void launch_ops(int type, const void* ops, int64_t count, const TermD* terms, const ChainTab& ct, const Bases& B,
                 int max_dense, cudaStream_t st);
 // One cooperative launch executing all waves of a TRSM/GEMM/chain plan with
@@ -45,7 +46,8 @@ void launch_logdet(const int64_t* offs, const int32_t* dims, int64_t count, cons
 
 // Device build of the cluster tree and block-cluster tree (tree.cu); returns
 // 0 or -1 on a CUDA failure.
-int device_tree_build(const double* d_xy, int64_t n, int leaf, double eta, cudaStream_t st,
+// adm: HLC_ADM_* admissibility rule; split: HLC_SPLIT_* bisection rule.
+int device_tree_build(const double* d_xy, int64_t n, int leaf, double eta, int adm, int split, cudaStream_t st,
                       std::vector<int32_t>& perm, std::vector<Cluster>& clusters, std::vector<Block>& blocks,
                       int* depth);
 

@@ -6,16 +6,19 @@
 //      positions;
 //   2. stable LSD radix sort of the 64-bit keys (8 passes of 8 bits), so that
 //      equal keys keep the callers' index order;
-//   3. geometric bisection level by level: per cluster the tight bounding box
-//      (block reduction), the longest axis (x on ties) split at its midpoint,
-//      coordinates <= midpoint to the left, stable; clusters of at most `leaf`
-//      points, or whose split would leave a side empty, are leaves; children
-//      are numbered breadth-first;
+//   3. bisection level by level: per cluster the tight bounding box (block
+//      reduction) and its longest axis (x on ties); the geometric rule puts
+//      the coordinates <= the axis midpoint to the left, the cardinality rule
+//      the floor(size/2) smallest coordinates (ties in position order);
+//      both partitions are stable; clusters of at most `leaf` points, or
+//      whose split would leave a side empty, are leaves; children are
+//      numbered breadth-first;
 //   4. block-cluster tree level by level over the lower triangle: a diagonal
 //      pair of a non-leaf splits into (1,1), (2,1), (2,2); an off-diagonal pair
-//      is admissible (low-rank) iff dist > 0 and min(diam) <= eta dist of the
-//      tight boxes, else dense when one side is a leaf, else split into its
-//      four child pairs.
+//      is admissible (low-rank) under the chosen rule -- dist > 0 and
+//      min(diam) <= eta dist of the tight boxes (standard), dist > 0 and
+//      max(diam) <= eta dist, or always (weak) -- else dense when one side is
+//      a leaf, else split into its four child pairs.
 //
 // The floating-point geometry uses explicitly rounded operations so that the
 // tree is bit-identical to the host build of the same rules.
@@ -219,9 +222,19 @@ __device__ __forceinline__ double block_min(double v, double* red) {
   return red[32];
 }
 
-// bbox, split decision and left count of every frontier cluster
+// Monotone 64-bit key of a double: a < b iff key(a) < key(b) (finite values,
+// -0 below +0).
+__device__ __forceinline__ uint64_t order_key(double v) {
+  const uint64_t b = (uint64_t)__double_as_longlong(v);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+// bbox, split decision and left count of every frontier cluster; for the
+// cardinality rule also the key of the median coordinate (thr) and how many
+// points with exactly that key go left (need)
 __global__ void k_bis_measure(DevCluster* cl, const int32_t* front, const double* px, const double* py, int leaf,
-                              int32_t* split, int64_t* nleft, int32_t* axis, double* mid) {
+                              int split_rule, int32_t* split, int64_t* nleft, int32_t* axis, double* mid,
+                              uint64_t* thr, int64_t* need) {
   __shared__ double red[33];
   const int32_t c = front[blockIdx.x];
   DevCluster C = cl[c];
@@ -245,11 +258,32 @@ __global__ void k_bis_measure(DevCluster* cl, const int32_t* front, const double
     md = ax == 0 ? __dmul_rn(0.5, __dadd_rn(mn0, mx0)) : __dmul_rn(0.5, __dadd_rn(mn1, mx1));
   }
   double cntl = 0.0;
-  if (size > leaf) {
+  uint64_t t_key = 0;
+  int64_t t_need = 0;
+  if (size > leaf && split_rule == HLC_SPLIT_GEOMETRIC) {
     const double* co = ax == 0 ? px : py;
     for (int64_t i = C.lo + threadIdx.x; i < C.hi; i += blockDim.x) cntl += (co[i] <= md) ? 1.0 : 0.0;
+    cntl = block_sum(cntl, red);
+  } else if (size > leaf) {
+    // the k-th smallest key, k = floor(size / 2): the smallest t with
+    // #{key <= t} >= k, found bit by bit from the top
+    const double* co = ax == 0 ? px : py;
+    const int64_t k = size / 2;
+    uint64_t t = 0;
+    for (int b = 63; b >= 0; --b) {
+      const uint64_t cand = t | ((1ull << b) - 1);  // t with the lower bits set: is #{key <= cand} >= k ?
+      double c = 0.0;
+      for (int64_t i = C.lo + threadIdx.x; i < C.hi; i += blockDim.x) c += order_key(co[i]) <= cand ? 1.0 : 0.0;
+      c = block_sum(c, red);
+      if (!(c >= (double)k)) t |= (1ull << b);  // the k-th key has bit b set
+    }
+    double below = 0.0;
+    for (int64_t i = C.lo + threadIdx.x; i < C.hi; i += blockDim.x) below += order_key(co[i]) < t ? 1.0 : 0.0;
+    below = block_sum(below, red);
+    t_key = t;
+    t_need = k - (int64_t)below;
+    cntl = (double)k;
   }
-  cntl = block_sum(cntl, red);
   if (threadIdx.x == 0) {
     C.bmin[0] = mn0;
     C.bmin[1] = mn1;
@@ -265,6 +299,8 @@ __global__ void k_bis_measure(DevCluster* cl, const int32_t* front, const double
     nleft[blockIdx.x] = nl;
     axis[blockIdx.x] = ax;
     mid[blockIdx.x] = md;
+    thr[blockIdx.x] = t_key;
+    need[blockIdx.x] = t_need;
   }
 }
 
@@ -281,25 +317,50 @@ __global__ void k_bis_scan(const int32_t* split, int nf, int32_t next_id, int32_
 
 // stable partition of every splitting cluster (through tmp), children records
 __global__ void k_bis_split(DevCluster* cl, const int32_t* front, const int32_t* split, const int64_t* nleft,
-                            const int32_t* axis, const double* mid, const int32_t* child0, double* px, double* py,
-                            int32_t* perm, double* tx, double* ty, int32_t* tp, int32_t* next_front) {
+                            const int32_t* axis, const double* mid, const uint64_t* thr, const int64_t* need,
+                            int split_rule, const int32_t* child0, double* px, double* py, int32_t* perm, double* tx,
+                            double* ty, int32_t* tp, int32_t* next_front) {
   __shared__ int sc[BS_THREADS];
-  __shared__ int64_t run_l, run_r;
+  __shared__ int64_t run_l, run_r, run_eq;
   if (!split[blockIdx.x]) return;
   const int32_t c = front[blockIdx.x];
   const DevCluster C = cl[c];
   const int64_t nl = nleft[blockIdx.x];
   const int ax = axis[blockIdx.x];
   const double md = mid[blockIdx.x];
+  const uint64_t tk = thr[blockIdx.x];
+  const int64_t nd = need[blockIdx.x];
   const double* co = ax == 0 ? px : py;
   if (threadIdx.x == 0) {
     run_l = 0;
     run_r = 0;
+    run_eq = 0;
   }
   __syncthreads();
   for (int64_t c0 = C.lo; c0 < C.hi; c0 += blockDim.x) {
     const int64_t i = c0 + threadIdx.x;
-    const int f = (i < C.hi && co[i] <= md) ? 1 : 0;
+    int f;
+    if (split_rule == HLC_SPLIT_GEOMETRIC) {
+      f = (i < C.hi && co[i] <= md) ? 1 : 0;
+    } else {
+      // below the median key: left; equal to it: left while fewer than
+      // `need` equal keys came before (position order); above: right
+      const uint64_t key = i < C.hi ? order_key(co[i]) : ~0ull;
+      const int eq = (i < C.hi && key == tk) ? 1 : 0;
+      sc[threadIdx.x] = eq;
+      __syncthreads();
+      for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+        const int v = threadIdx.x >= o ? sc[threadIdx.x - o] : 0;
+        __syncthreads();
+        sc[threadIdx.x] += v;
+        __syncthreads();
+      }
+      const int64_t eq_before = run_eq + sc[threadIdx.x] - eq;
+      const int eq_tot = sc[blockDim.x - 1];
+      f = (i < C.hi && (key < tk || (eq && eq_before < nd))) ? 1 : 0;
+      __syncthreads();
+      if (threadIdx.x == 0) run_eq += eq_tot;
+    }
     sc[threadIdx.x] = f;
     __syncthreads();
     // inclusive scan (Hillis-Steele) over the chunk
@@ -372,7 +433,7 @@ __device__ __forceinline__ double dist_dev(const DevCluster& a, const DevCluster
 
 // type and child count of every frontier block
 __global__ void k_blk_classify(DevBlock* bl, const int32_t* front, int nf, const DevCluster* cl, double eta,
-                               int32_t* nchild) {
+                               int adm_rule, int32_t* nchild) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nf) return;
   DevBlock& B = bl[front[i]];
@@ -391,7 +452,13 @@ __global__ void k_blk_classify(DevBlock* bl, const int32_t* front, int nf, const
   } else {
     B.diag = 0;
     const double d = dist_dev(R, S);
-    const bool adm = d > 0.0 && fmin(diam_dev(R), diam_dev(S)) <= __dmul_rn(eta, d);
+    bool adm;
+    if (adm_rule == HLC_ADM_WEAK)
+      adm = true;
+    else if (adm_rule == HLC_ADM_MAXDIAM)
+      adm = d > 0.0 && fmax(diam_dev(R), diam_dev(S)) <= __dmul_rn(eta, d);
+    else
+      adm = d > 0.0 && fmin(diam_dev(R), diam_dev(S)) <= __dmul_rn(eta, d);
     if (adm) {
       B.type = BT_LR;
     } else if (lr || ls) {
@@ -457,7 +524,7 @@ __global__ void k_blk_expand(DevBlock* bl, const int32_t* front, int nf, const D
     if ((x) != cudaSuccess) return -1;         \
   } while (0)
 
-int device_tree_build(const double* d_xy, int64_t n, int leaf, double eta, cudaStream_t st,
+int device_tree_build(const double* d_xy, int64_t n, int leaf, double eta, int adm, int split_rule, cudaStream_t st,
                       std::vector<int32_t>& perm, std::vector<Cluster>& clusters, std::vector<Block>& blocks,
                       int* depth) {
   const int nb_box = 304;
@@ -471,6 +538,8 @@ int device_tree_build(const double* d_xy, int64_t n, int leaf, double eta, cudaS
   int32_t *tp = nullptr, *front = nullptr, *nfront = nullptr, *dsplit = nullptr, *daxis = nullptr, *dchild0 = nullptr,
           *dn = nullptr;
   int64_t* dnl = nullptr;
+  int64_t* dneed = nullptr;
+  uint64_t* dthr = nullptr;
   DevCluster* dcl = nullptr;
   DevBlock* dbl = nullptr;
   const int64_t maxcl = 2 * n + 1;
@@ -497,7 +566,8 @@ int device_tree_build(const double* d_xy, int64_t n, int leaf, double eta, cudaS
         cudaMalloc(&tp, n * 4) || cudaMalloc(&dcl, maxcl * sizeof(DevCluster)) ||
         cudaMalloc(&front, maxcl * 4) || cudaMalloc(&nfront, maxcl * 4) || cudaMalloc(&dsplit, maxcl * 4) ||
         cudaMalloc(&daxis, maxcl * 4) || cudaMalloc(&dchild0, maxcl * 4) || cudaMalloc(&dmid, maxcl * 8) ||
-        cudaMalloc(&dnl, maxcl * 8) || cudaMalloc(&dn, 8)) {
+        cudaMalloc(&dnl, maxcl * 8) || cudaMalloc(&dn, 8) || cudaMalloc(&dthr, maxcl * 8) ||
+        cudaMalloc(&dneed, maxcl * 8)) {
       rc = -1;
       break;
     }
@@ -512,10 +582,11 @@ int device_tree_build(const double* d_xy, int64_t n, int leaf, double eta, cudaS
     cudaMemcpyAsync(front, &zero, 4, cudaMemcpyHostToDevice, st);
     int32_t nf = 1, ncl = 1, lev = 0;
     while (nf > 0) {
-      k_bis_measure<<<nf, BS_THREADS, 0, st>>>(dcl, front, px, py, leaf, dsplit, dnl, daxis, dmid);
+      k_bis_measure<<<nf, BS_THREADS, 0, st>>>(dcl, front, px, py, leaf, split_rule, dsplit, dnl, daxis, dmid, dthr,
+                                             dneed);
       k_bis_scan<<<1, 1, 0, st>>>(dsplit, nf, ncl, dchild0, dn);
-      k_bis_split<<<nf, BS_THREADS, 0, st>>>(dcl, front, dsplit, dnl, daxis, dmid, dchild0, px, py, i0, tx, ty, tp,
-                                           nfront);
+      k_bis_split<<<nf, BS_THREADS, 0, st>>>(dcl, front, dsplit, dnl, daxis, dmid, dthr, dneed, split_rule, dchild0, px,
+                                           py, i0, tx, ty, tp, nfront);
       int32_t ns = 0;
       cudaMemcpyAsync(&ns, dn, 4, cudaMemcpyDeviceToHost, st);
       if (cudaStreamSynchronize(st) != cudaSuccess) {
@@ -561,7 +632,7 @@ int device_tree_build(const double* d_xy, int64_t n, int leaf, double eta, cudaS
     nchild = dsplit;
     first = dchild0;
     while (nf > 0) {
-      k_blk_classify<<<(nf + 255) / 256, 256, 0, st>>>(dbl, front, nf, dcl, eta, nchild);
+      k_blk_classify<<<(nf + 255) / 256, 256, 0, st>>>(dbl, front, nf, dcl, eta, adm, nchild);
       k_blk_scan<<<1, 1, 0, st>>>(nchild, nf, nbl, first, dn);
       int32_t tot = 0;
       cudaMemcpyAsync(&tot, dn, 4, cudaMemcpyDeviceToHost, st);
@@ -626,6 +697,8 @@ int device_tree_build(const double* d_xy, int64_t n, int leaf, double eta, cudaS
   cudaFree(dchild0);
   cudaFree(dmid);
   cudaFree(dnl);
+  cudaFree(dthr);
+  cudaFree(dneed);
   cudaFree(dn);
   cudaFree(dcl);
   cudaFree(dbl);

@@ -323,8 +323,8 @@ __device__ __forceinline__ void phase_mark(unsigned long long* ph, int slot, lon
 }
 
 template <class T, class C>
-__device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, C* M, C* W, C* J, C* X, C* Cu, C* Cv,
-                        CoreShared<C>& cs, int* status,
+__device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, int kfix, C* M, C* W, C* J, C* X, C* Cu,
+                        C* Cv, CoreShared<C>& cs, int* status,
                         unsigned long long* ph = nullptr) {
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
   long long t0 = clock64();
@@ -585,6 +585,7 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, C
       record_error(status, DEV_BAD, 1);
       k = 0;
     }
+    if (kfix > 0 && k > kfix) k = kfix;  // fixed-rank mode
     if (k > kcap) {
       record_error(status, DEV_RANK, k);
       k = kcap;
@@ -820,7 +821,7 @@ __global__ void __launch_bounds__(TR_THREADS, sizeof(T) == 4 ? 2 : 1) k_trunc(co
         qr_stream<T>([&](int r, int c) { return cat_value(B, op, cat, 1, r, c); }, op.n, K, Pv, sC, sh);
       }
       phase_mark(B.phase, 2, tp);
-      tr_core<T, C>(Pu, Pv, K, op.eps, op.kcap, M, W, J, X, Cu, Cv, cs, B.status, B.phase);
+      tr_core<T, C>(Pu, Pv, K, op.eps, op.kcap, op.kfix, M, W, J, X, Cu, Cv, cs, B.status, B.phase);
       tp = clock64();
       const int k = cs.k;
       // algorithmic flops of the batch: two streamed R factors and the apply
@@ -921,7 +922,7 @@ __global__ void __cluster_dims__(TR_CL, 1, 1) __launch_bounds__(TR_THREADS, size
           Rv[i + (int64_t)j * TR_KT] = fv[i + (int64_t)j * TR_KT];
         }
         __syncthreads();
-        tr_core<T, C>(Ru, Rv, K, op.eps, op.kcap, M, W, J, X, Cu0, Cv0, cs, B.status);
+        tr_core<T, C>(Ru, Rv, K, op.eps, op.kcap, op.kfix, M, W, J, X, Cu0, Cv0, cs, B.status);
         if (threadIdx.x == 0) flag0[0] = cs.k;
       }
       __threadfence();

@@ -37,10 +37,15 @@ class hlc_theta(ctypes.Structure):
                 ("nugget", ctypes.c_double)]
 
 
+HLC_ADM_STANDARD, HLC_ADM_MAXDIAM, HLC_ADM_WEAK = 0, 1, 2
+HLC_SPLIT_GEOMETRIC, HLC_SPLIT_CARDINALITY = 0, 1
+
+
 class hlc_params(ctypes.Structure):
     _fields_ = [("leaf", ctypes.c_int), ("eta", ctypes.c_double), ("eps", ctypes.c_double),
                 ("precision", ctypes.c_int), ("refine_tol", ctypes.c_double), ("refine_maxit", ctypes.c_int),
-                ("kmax", ctypes.c_int)]
+                ("kmax", ctypes.c_int), ("admissibility", ctypes.c_int), ("split", ctypes.c_int),
+                ("fixed_rank", ctypes.c_int)]
 
 
 class hlc_result(ctypes.Structure):
@@ -164,11 +169,13 @@ def _check(st, what):
         raise HlcError(st, what)
 
 
-def params(leaf=64, eta=2.0, eps=1e-6, precision=HLC_FP64, refine_tol=1e-12, refine_maxit=100, kmax=64):
+def params(leaf=64, eta=2.0, eps=1e-6, precision=HLC_FP64, refine_tol=1e-12, refine_maxit=100, kmax=64,
+           admissibility=HLC_ADM_STANDARD, split=HLC_SPLIT_GEOMETRIC, fixed_rank=0):
     p = hlc_params()
     hlc_default_params(ctypes.byref(p))
     p.leaf, p.eta, p.eps, p.precision = int(leaf), float(eta), float(eps), int(precision)
     p.refine_tol, p.refine_maxit, p.kmax = float(refine_tol), int(refine_maxit), int(kmax)
+    p.admissibility, p.split, p.fixed_rank = int(admissibility), int(split), int(fixed_rank)
     return p
 
 
@@ -343,13 +350,15 @@ class Tree:
     """hlc_build_tree and the calls on a tree."""
 
     def __init__(self, ctx, xy, leaf=64, eta=2.0, eps=1e-6, precision=HLC_FP64, refine_tol=1e-12,
-                 refine_maxit=100, kmax=64):
+                 refine_maxit=100, kmax=64, admissibility=HLC_ADM_STANDARD, split=HLC_SPLIT_GEOMETRIC,
+                 fixed_rank=0):
         self.ctx = ctx
         if not hasattr(xy, "data_ptr"):
             xy = np.ascontiguousarray(xy, dtype=np.float64)
         self._xy = xy
         self.n = int(xy.shape[0])
-        self.p = params(leaf, eta, eps, precision, refine_tol, refine_maxit, kmax)
+        self.p = params(leaf, eta, eps, precision, refine_tol, refine_maxit, kmax, admissibility, split,
+                        fixed_rank)
         h = _vp()
         _check(hlc_build_tree(ctx.h, _ptr(xy), self.n, ctypes.byref(self.p), ctypes.byref(h)), "hlc_build_tree")
         self.h = h

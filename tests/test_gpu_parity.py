@@ -418,3 +418,28 @@ def test_variance_scaling_invariance(ctx, hlc):
     r1 = t.loglik(hlc.theta(a, 0.05, 1.5, a * 1e-4), z)
     assert abs(r1["logdet"] - (r0["logdet"] + n * math.log(a))) <= 1e-9 * abs(r0["logdet"])
     assert abs(r1["quad"] - r0["quad"] / a) <= 1e-9 * r0["quad"]
+
+
+def test_aca_rank_above_64(ctx, hlc):
+    # Admissible blocks whose ACA needs more than 64 crosses (a wide
+    # admissibility, eta = 8, and eps = 1e-14): with a rank capacity of 64
+    # the assembly stops with HLC_ERR_RANK instead of accepting a block that
+    # has not reached eps; with 128 it completes, and C~ agrees with the
+    # oracle's (ACA without a rank cap) entry by entry.
+    n, eps, eta = 6000, 1e-14, 8.0
+    xy = inputs.points(n, 9100)
+    th = hlc.theta(1.0, 0.5, 0.5, 1e-4)
+    with pytest.raises(hlc.HlcError) as e:
+        ctx.build_tree(xy, leaf=64, eta=eta, eps=eps, kmax=64).assemble(th)
+    assert e.value.status == hlc.HLC_ERR_RANK
+    t = ctx.build_tree(xy, leaf=64, eta=eta, eps=eps, kmax=128)
+    C = t.assemble(th)
+    rg = C.ranks()
+    assert rg.max() > 64
+    H = oracle.HOracle(xy, leaf=64, eta=eta)
+    H.assemble(1.0, 0.5, 0.5, 1e-4, eps)
+    ro = H.ranks(0)
+    assert np.all((rg < 0) == (ro < 0))
+    assert np.max(np.abs(rg - ro)) <= 2
+    Cg, Co = C.expand(), H.expand(0)
+    assert np.abs(Cg - Co).max() <= 1e-11 * np.abs(Co).max()

@@ -1,0 +1,77 @@
+"""Variants of the block structure and the rank (Sec. 2.2, App. A, Tables 2
+and 3) on the GPU against the CPU oracle: max-diameter and weak
+admissibility, the cardinality (median) split, and the fixed-rank mode."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1709_08625_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hlc():
+    from paper_1709_08625_gb300 import build
+
+    build.build()
+    from paper_1709_08625_gb300 import hlc as h
+
+    return h
+
+
+@pytest.fixture(scope="module")
+def ctx(hlc):
+    c = hlc.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("n,leaf,eta,adm,split", [(3001, 32, 2.0, 1, 0), (3001, 32, 2.0, 2, 0), (3001, 32, 2.0, 0, 1),
+                                                  (777, 16, 4.0, 1, 1), (65537, 64, 2.0, 0, 1),
+                                                  (20000, 64, 2.0, 2, 1)])
+def test_variant_trees_match_oracle(ctx, n, leaf, eta, adm, split):
+    xy = inputs.points(n, 8000 + n)
+    xy[10:30] = xy[3]  # coincident points: the median split still halves
+    t = ctx.build_tree(xy, leaf=leaf, eta=eta, admissibility=adm, split=split)
+    H = oracle.HOracle(xy, leaf=leaf, eta=eta, admissibility=adm, split=split)
+    np.testing.assert_array_equal(t.perm(), H.perm())
+    np.testing.assert_array_equal(t.leaf_blocks(), H.leaf_blocks())
+
+
+@pytest.mark.parametrize("adm,split,nu", [(1, 0, 0.5), (2, 0, 0.5), (0, 1, 1.5), (2, 1, 0.325)])
+def test_variant_loglik_vs_oracle(ctx, hlc, adm, split, nu):
+    n, eps = 4000, 1e-7
+    xy = inputs.points(n, 8100)
+    z = inputs.normal(n, 8101)
+    th = (1.0, 0.05, nu, 1e-4)
+    t = ctx.build_tree(xy, leaf=64, eps=eps, kmax=128, admissibility=adm, split=split)
+    r = t.loglik(hlc.theta(*th), z)
+    ho = oracle.h_loglik(xy, z, *th, eps, leaf=64, admissibility=adm, split=split)
+    assert abs(r["loglik"] - ho["loglik"]) / n <= 1e-7
+    assert abs(r["logdet"] - ho["logdet"]) / n <= 1e-7
+
+
+@pytest.mark.parametrize("k", [10, 16, 24])
+def test_fixed_rank_vs_oracle(ctx, hlc, k):
+    # fixed-rank mode (Tables 2 and 3): at most k columns in every low-rank
+    # block of C~ and of the factor; the assembled C~ and the likelihood
+    # agree with the oracle in the same mode
+    n = 3000
+    xy = inputs.points(n, 8200)
+    z = inputs.normal(n, 8201)
+    th = (1.0, 0.25, 0.5, 1e-2)
+    t = ctx.build_tree(xy, leaf=32, eps=1e-14, kmax=64, fixed_rank=k)
+    C = t.assemble(hlc.theta(*th))
+    rg = C.ranks()
+    assert rg.max() == k
+    H = oracle.HOracle(xy, leaf=32, fixed_rank=k)
+    H.assemble(*th, 1e-14)
+    np.testing.assert_array_equal(rg, H.ranks(0))
+    Co = H.expand(0)
+    assert np.abs(C.expand() - Co).max() <= 1e-8 * np.abs(Co).max()
+    L = t.cholesky(C)
+    assert L.ranks().max() <= k
+    r = t.loglik(hlc.theta(*th), z)
+    ho = oracle.h_loglik(xy, z, *th, 1e-14, leaf=32, fixed_rank=k)
+    assert abs(r["loglik"] - ho["loglik"]) / n <= 1e-7

@@ -472,3 +472,95 @@ def test_factor_product_reproduces_covariance():
     # and against the expanded factor (the lower triangle of the blocks)
     Le = H.expand(1)
     np.testing.assert_allclose(H.lmatvec(x), Le @ x, rtol=0, atol=1e-12 * np.abs(Le @ x).max())
+
+
+# ----------------------------------------------------------------------------
+# Variants of the block structure and of the rank (Sec. 2.2, App. A,
+# Tables 2 and 3)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("n,leaf", [(777, 16), (3001, 32)])
+def test_cardinality_split_halves_at_the_median(n, leaf):
+    # "two (equal sized) sub-sets": each split puts floor(size/2) points,
+    # those with the smallest coordinates along the longest bbox axis, left
+    xy = inputs.points(n, 4200 + n)
+    xy[10:40, 0] = xy[5, 0]  # ties on the split coordinate
+    Hh = oracle.HOracle(xy, leaf=leaf, split=1)
+    perm = Hh.perm()
+    assert sorted(perm) == list(range(n))
+    pts = xy[perm]
+    lohi, bbox, lev, isleaf = Hh.clusters()
+    nsplit = 0
+    for i, (lo, hi) in enumerate(lohi):
+        if isleaf[i]:
+            assert hi - lo <= leaf
+            continue
+        nsplit += 1
+        kids = [j for j, (a, b) in enumerate(lohi) if lev[j] == lev[i] + 1 and a >= lo and b <= hi]
+        k0, k1 = sorted(kids, key=lambda j: lohi[j][0])
+        assert lohi[k0][1] - lo == (hi - lo) // 2
+        ext = bbox[i, 2:] - bbox[i, :2]
+        ax = 0 if ext[0] >= ext[1] else 1
+        assert pts[lo:lohi[k0][1], ax].max() <= pts[lohi[k1][0]:hi, ax].min()
+    assert nsplit > 0
+
+
+@pytest.mark.parametrize("adm,eta", [(1, 2.0), (1, 4.0), (2, 2.0)])
+def test_block_tree_admissibility_variants(adm, eta):
+    n, leaf = 2500, 32
+    xy = inputs.points(n, 4300)
+    Hh = oracle.HOracle(xy, leaf=leaf, eta=eta, admissibility=adm)
+    pts = xy[Hh.perm()]
+    cover = np.zeros((n, n), dtype=np.int32)
+    nlr = 0
+    for r0, r1, c0, c1, t in Hh.leaf_blocks():
+        cover[r0:r1, c0:c1] += 1
+        R, S = pts[r0:r1], pts[c0:c1]
+        diam = lambda P: np.hypot(*np.ptp(P, axis=0))
+        gap = np.maximum(0, np.maximum(R.min(0) - S.max(0), S.min(0) - R.max(0)))
+        dist = np.hypot(*gap)
+        if adm == 1:
+            assert bool(dist > 0 and max(diam(R), diam(S)) <= eta * dist) == (t == 1)
+        else:  # weak: every block of two distinct clusters is low-rank
+            assert (t == 1) == (r0 != c0)
+        nlr += t == 1
+    low = np.tril(np.ones((n, n), dtype=bool))
+    assert np.all(cover[low] == 1) and nlr > 0
+    # max-diam is stricter than the standard rule: fewer low-rank leaves
+    if adm == 1:
+        std = oracle.HOracle(xy, leaf=leaf, eta=eta)
+        assert (std.leaf_blocks()[:, 4] == 1).sum() >= nlr
+
+
+@pytest.mark.parametrize("adm,split", [(1, 0), (2, 0), (0, 1), (2, 1)])
+def test_variant_h_loglik_vs_dense(adm, split):
+    # every variant approximates the same eq. (1)
+    n = 1500
+    xy = inputs.points(n, 4400)
+    th = (1.0, 0.1, 0.5, 1e-4)
+    z = oracle.dense_chol_apply(xy, inputs.normal(n, 4401), *th)
+    Ld = oracle.dense_loglik(xy, z, *th)[0]
+    r = oracle.h_loglik(xy, z, *th, 1e-8, leaf=32, admissibility=adm, split=split)
+    assert abs(r["loglik"] - Ld) / n <= 1e-6
+
+
+def test_fixed_rank_caps_ranks_and_error_falls_with_k():
+    # Tables 2 and 3: fixed rank k, no nugget; ranks never exceed k and the
+    # approximation error falls as k grows
+    n = 1200
+    xy = inputs.points(n, 4500)
+    th = (1.0, 0.25, 0.5, 0.0)
+    C = oracle.dense_cov(xy, *th)
+    errs = []
+    for k in (4, 8, 16):
+        Hh = oracle.HOracle(xy, leaf=32, fixed_rank=k)
+        Hh.assemble(*th, 1e-14)
+        r = Hh.ranks(0)
+        assert r.max() <= k
+        errs.append(np.linalg.norm(C - Hh.expand(0), 2))
+    assert errs[0] > errs[1] > errs[2]
+    # a cap above every adaptive rank changes nothing
+    Ha = oracle.HOracle(xy, leaf=32)
+    Ha.assemble(*th, 1e-6)
+    Hk = oracle.HOracle(xy, leaf=32, fixed_rank=int(Ha.ranks(0).max()) + 5)
+    Hk.assemble(*th, 1e-6)
+    np.testing.assert_array_equal(Ha.expand(0), Hk.expand(0))
