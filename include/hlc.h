@@ -41,9 +41,9 @@
  *                     as one cooperative launch
  *   HLC_GRAPHS=0      launch the op waves directly instead of replaying CUDA
  *                     graphs
- *   HLC_CHAINS=0      plan the solves of small diagonal blocks op by op
- *                     instead of as chains run by one CTA each (same result,
- *                     bit for bit)
+ *   HLC_CHAINS=1      plan the solve of every small diagonal block as one
+ *                     chain op run by one CTA instead of op by op (same
+ *                     result, bit for bit)
  *   HLC_PROFILE=1     time every op launch (synchronising) and print a summary
  *                     at exit
  *   HLC_PHASES=1      count clock cycles per phase of the truncation kernel and
@@ -149,6 +149,7 @@ const char* hlc_strerror(int status);
 /* Create a context on CUDA device `device` (its own stream and workspaces).
  * HLC_ERR_CUDA if the device is absent. */
 int hlc_create(hlc_ctx** out, int device);
+/* Destroy a context.  Free its trees and H-matrices first: they refer to it. */
 void hlc_destroy(hlc_ctx* ctx);
 
 /*

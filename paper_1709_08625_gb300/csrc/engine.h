@@ -35,10 +35,10 @@ void layout(HTree& T, int kmax);
 void plan_cholesky(HTree& T, Plan& P, bool accumulate = false);
 // chains: the solve of every subdivided diagonal block of at most 1024 rows
 // becomes one op (a chain run by one CTA)
-void plan_solve(HTree& T, Plan& P, int trans, int64_t voff, int64_t ncols, bool chains = true);
+void plan_solve(HTree& T, Plan& P, int trans, int64_t voff, int64_t ncols, bool chains = false);
 void plan_matvec(HTree& T, Plan& P, int64_t xoff, int64_t yoff, int64_t ncols);
 // X := L X (trans 0) or L^T X (trans 1), in place, L the lower factor
-void plan_trmv(HTree& T, Plan& P, int trans, int64_t voff, int64_t ncols, bool chains = true);
+void plan_trmv(HTree& T, Plan& P, int trans, int64_t voff, int64_t ncols, bool chains = false);
 void plan_recompress(HTree& T, Plan& P);
 // Bounds check of every view against the buffer sizes (in doubles) and of
 // every rank slot against the rank array's length.

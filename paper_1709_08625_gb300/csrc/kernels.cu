@@ -239,6 +239,10 @@ __global__ void __launch_bounds__(ACA_THREADS) k_aca(const LrAsm* blks, int64_t 
   }
 }
 
+// loads staged through registers per thread before their stores to shared
+// memory (independent loads in flight)
+constexpr int LD_BATCH = 16;
+
 // ---------------------------------------------------------------------------
 // POTRF: dense lower Cholesky of a diagonal leaf (n <= 128), right-looking.
 // ---------------------------------------------------------------------------
@@ -251,9 +255,18 @@ __global__ void k_potrf(const OpPotrf* ops, int64_t count, Bases B) {
     if (B.flops && threadIdx.x == 0) atomicAdd(B.flops + OP_POTRF, (double)n * n * n / 3.0);
     double* A = vptr(B, op.A);
     const int64_t ld = op.A.cs;
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-      const int i = e % n, j = e / n;
-      sm[e] = A[i + j * ld];
+    for (int e0 = threadIdx.x; e0 < n * n; e0 += LD_BATCH * blockDim.x) {
+      double v[LD_BATCH];
+#pragma unroll
+      for (int u = 0; u < LD_BATCH; ++u) {
+        const int e = e0 + u * blockDim.x;
+        v[u] = e < n * n ? A[(e % n) + (e / n) * ld] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < LD_BATCH; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e < n * n) sm[e] = v[u];
+      }
     }
     __syncthreads();
     // diagonal before this block's elimination (pivot tolerance reference)
@@ -309,9 +322,19 @@ __device__ void do_trsm(const OpTrsm& op, const Bases& B, T* sL) {
   if (B.flops && threadIdx.x == 0) atomicAdd(B.flops + OP_TRSM, (double)n * n * c);
   const double* L = vptr(B, op.L);
   T* sInv = sL + n * n;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    const int i = e % n, j = e / n;
-    sL[e] = (T)L[i * op.L.rs + j * op.L.cs];
+  // the block through registers, LD_BATCH loads in flight per thread
+  for (int e0 = threadIdx.x; e0 < n * n; e0 += LD_BATCH * blockDim.x) {
+    T v[LD_BATCH];
+#pragma unroll
+    for (int u = 0; u < LD_BATCH; ++u) {
+      const int e = e0 + u * blockDim.x;
+      v[u] = e < n * n ? (T)L[(e % n) * op.L.rs + (e / n) * op.L.cs] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < LD_BATCH; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e < n * n) sL[e] = v[u];
+    }
   }
   for (int i = threadIdx.x; i < n; i += blockDim.x) sInv[i] = T(1) / (T)L[i * op.L.rs + i * op.L.cs];
   __syncthreads();
@@ -402,11 +425,20 @@ struct GemmSmem {
   T Bs[GB_K][GB_N + 1];
 };
 
-// Y (m x 1) = beta Y + alpha A x: a warp per row where the rows of A are
-// contiguous (lanes stride along the row), a thread per row otherwise
-// (consecutive threads read consecutive rows); fixed summation order.
+// Y (m x 1) = beta Y + alpha A x, in a fixed summation order.  Where the
+// rows of A are contiguous, a warp per row (lanes stride along the row).
+// Otherwise (column-major A) the CTA takes GV_ROWS rows at a time and splits
+// the inner dimension into blockDim / GV_ROWS interleaved parts, one thread
+// per (row, part): every thread issues GV_UNROLL independent loads before it
+// uses them, so that a product over a block in HBM waits for about one
+// memory latency instead of one per column; the parts are then added in
+// part order through shared memory.
+constexpr int GV_ROWS = 64;
+constexpr int GV_UNROLL = 8;
+
 template <class T>
 __device__ void do_gemv(const OpGemm& op, const Bases& B, int m, int k, double* Y, const double* A) {
+  __shared__ T gv_red[256];
   const bool ones = op.B.buf == MV_ONES;
   const double* x = ones ? nullptr : vptr(B, op.B);
   const int64_t xs = op.B.rs;
@@ -426,19 +458,39 @@ __device__ void do_gemv(const OpGemm& op, const Bases& B, int m, int k, double* 
         *yp = op.beta ? *yp + v : v;
       }
     }
-  } else {
-    for (int i = tid; i < m; i += blockDim.x) {
+    return;
+  }
+  const int P = (int)blockDim.x / GV_ROWS;  // parts of the inner dimension
+  const int r = tid % GV_ROWS, p = tid / GV_ROWS;
+  for (int r0 = 0; r0 < m; r0 += GV_ROWS) {
+    const int i = r0 + r;
+    T acc = T(0);
+    if (i < m && p < P) {
       const double* a = A + (int64_t)i * op.A.rs;
-      T acc = T(0);
-      if (ones)
-        for (int q = 0; q < k; ++q) acc += (T)a[q * op.A.cs];
-      else
-        for (int q = 0; q < k; ++q) acc += (T)a[q * op.A.cs] * (T)x[q * xs];
+      for (int q0 = p; q0 < k; q0 += GV_UNROLL * P) {
+        T av[GV_UNROLL], xv[GV_UNROLL];
+#pragma unroll
+        for (int u = 0; u < GV_UNROLL; ++u) {
+          const int q = q0 + u * P;
+          av[u] = q < k ? (T)a[(int64_t)q * op.A.cs] : T(0);
+          xv[u] = q < k ? (ones ? T(1) : (T)x[(int64_t)q * xs]) : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < GV_UNROLL; ++u) acc += av[u] * xv[u];
+      }
+    }
+    __syncthreads();
+    if (tid < GV_ROWS * P) gv_red[tid] = acc;
+    __syncthreads();
+    if (p == 0 && i < m) {
+      T s = T(0);
+      for (int q = 0; q < P; ++q) s += gv_red[q * GV_ROWS + r];
       double* yp = Y + (int64_t)i * op.Y.rs;
-      const double v = op.alpha * (double)acc;
+      const double v = op.alpha * (double)s;
       *yp = op.beta ? *yp + v : v;
     }
   }
+  __syncthreads();
 }
 
 template <class T>

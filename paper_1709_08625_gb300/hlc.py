@@ -242,10 +242,20 @@ class Context:
         h = _vp()
         _check(hlc_create(ctypes.byref(h), int(device)), "hlc_create")
         self.h = h
+        self._children = weakref.WeakSet()  # trees and matrices made on this context
         _LIVE["ctxs"].add(self)
 
     def close(self):
+        """Destroy the context, after freeing the trees and matrices made on
+        it (the C ABI requires them to go first)."""
         if getattr(self, "h", None):
+            kids = list(getattr(self, "_children", ()))
+            for obj in kids:
+                if isinstance(obj, HMat):
+                    obj.free()
+            for obj in kids:
+                if isinstance(obj, Tree):
+                    obj.free()
             hlc_destroy(self.h)
             self.h = None
 
@@ -305,6 +315,7 @@ class HMat:
     def __init__(self, ctx, tree, h):
         self.ctx, self.tree, self.h = ctx, tree, h
         _LIVE["mats"].add(self)
+        ctx._children.add(self)
 
     def free(self):
         if getattr(self, "h", None):
@@ -363,6 +374,7 @@ class Tree:
         _check(hlc_build_tree(ctx.h, _ptr(xy), self.n, ctypes.byref(self.p), ctypes.byref(h)), "hlc_build_tree")
         self.h = h
         _LIVE["trees"].add(self)
+        ctx._children.add(self)
         info = self.info()
         self.nleaves = info["dense"] + info["lowrank"]
 
