@@ -39,6 +39,9 @@
  *                     truncated at once)
  *   HLC_PERSISTENT=0  run triangular solves and matvecs wave by wave instead of
  *                     as one cooperative launch
+ *   HLC_FLOW=0        in that cooperative launch, separate the waves by a grid
+ *                     barrier instead of starting every op once its own
+ *                     producers are done (same result, bit for bit)
  *   HLC_GRAPHS=0      launch the op waves directly instead of replaying CUDA
  *                     graphs
  *   HLC_CHAINS=1      plan the solve of every small diagonal block as one

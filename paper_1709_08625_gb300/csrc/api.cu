@@ -170,6 +170,11 @@ int upload_plan(Plan& P) {
   if ((st = upload(&P.d_potrf, P.potrf))) return st;
   if ((st = upload(&P.d_trunc, P.trunc))) return st;
   if ((st = upload(&P.d_terms, P.terms))) return st;
+  if ((st = upload(&P.d_flow, P.flow))) return st;
+  if ((st = upload(&P.d_npred, P.npred))) return st;
+  if ((st = upload(&P.d_succ_off, P.succ_off))) return st;
+  if ((st = upload(&P.d_succ, P.succ))) return st;
+  if (!P.flow.empty()) CK(cudaMalloc(&P.d_count, P.flow.size() * sizeof(int32_t)));
   if ((st = upload(&P.d_chain, P.chain))) return st;
   if ((st = upload(&P.d_citems, P.citems))) return st;
   if ((st = upload(&P.d_ctrsm, P.ctrsm))) return st;
@@ -187,6 +192,16 @@ void free_plan(Plan& P) {
   cudaFree(P.d_potrf);
   cudaFree(P.d_trunc);
   cudaFree(P.d_terms);
+  cudaFree(P.d_flow);
+  cudaFree(P.d_npred);
+  cudaFree(P.d_succ_off);
+  cudaFree(P.d_succ);
+  cudaFree(P.d_count);
+  P.d_flow = nullptr;
+  P.d_npred = nullptr;
+  P.d_succ_off = nullptr;
+  P.d_succ = nullptr;
+  P.d_count = nullptr;
   cudaFree(P.d_chain);
   cudaFree(P.d_citems);
   cudaFree(P.d_ctrsm);
@@ -263,6 +278,22 @@ bool chains_enabled() {
   return on;
 }
 
+// TRSM/GEMM plans run dependency-driven (k_flow) unless HLC_FLOW=0, which
+// keeps the wave-by-wave persistent kernel (k_waves)
+bool flow_enabled() {
+  static const bool on = !(getenv("HLC_FLOW") && getenv("HLC_FLOW")[0] == '0');
+  return on;
+}
+
+// One persistent launch of a TRSM/GEMM plan: dependency-driven when the plan
+// has its dataflow form, else wave by wave.  0 or -1 (launch unavailable).
+int launch_persistent(const Plan& P, const Bases& B, GridBar* gb, int md, int per, cudaStream_t st) {
+  if (flow_enabled() && P.d_flow && P.d_count)
+    return launch_flow(P.d_flow, (int64_t)P.flow.size(), P.d_npred, P.d_succ_off, P.d_succ, P.d_count, P.d_trsm,
+                       P.d_gemm, B, gb, md, per, st);
+  return launch_waves(P.d_waves, (int)P.waves.size(), P.d_trsm, P.d_gemm, P.d_chain, P.chains(), B, gb, md, per, st);
+}
+
 bool persistent_enabled() {
   static const bool on = !(getenv("HLC_PERSISTENT") && getenv("HLC_PERSISTENT")[0] == '0');
   return on;
@@ -297,8 +328,7 @@ void run_plan(hlc_tree* t, const Plan& P, const Bases& B, cudaStream_t st) {
       }
       if (e0 && e1) cudaEventRecord(e0, st);
     }
-    if (launch_waves(P.d_waves, (int)P.waves.size(), P.d_trsm, P.d_gemm, P.d_chain, P.chains(), B, c->d_gridbar, md,
-                     per, st) == 0) {
+    if (launch_persistent(P, B, c->d_gridbar, md, per, st) == 0) {
       c->launches += 1;
       c->persistent_launches += 1;
       if (cand >= 0) {
@@ -1667,8 +1697,7 @@ int hlc_matvec_noalloc(hlc_ctx* c, const hlc_hmat* C, const double* x, double* y
   const int md = (int)std::max<int64_t>(t->T.max_dense_dim, t->T.leaf);
   bool done = false;
   if (c->persistent && !c->profiling && !g_prof.on && persistent_enabled()) {
-    if (launch_waves(t->mv.d_waves, (int)t->mv.waves.size(), t->mv.d_trsm, t->mv.d_gemm, t->mv.d_chain,
-                     t->mv.chains(), B, c->d_gridbar, md, t->mv.tuned_per_sm, c->stream) == 0) {
+    if (launch_persistent(t->mv, B, c->d_gridbar, md, t->mv.tuned_per_sm, c->stream) == 0) {
       done = true;
       c->launches += 1;
       c->persistent_launches += 1;

@@ -91,6 +91,10 @@ struct Rect {
 struct Acc {
   Rect rc;
   int32_t lw, lr;  // wave of the last write / latest read
+  // op-level dependencies (tracked for the dataflow plans): the op that
+  // last wrote the region and the ops that read it since
+  int64_t wop = -1;
+  std::vector<int64_t> rops;
 };
 
 struct Obj {
@@ -273,19 +277,44 @@ struct Planner {
   static Dim dim(int64_t n, int32_t slot) { return Dim{(int32_t)n, slot}; }
 
   // ---- dependency analysis ----
+  // Op-level dependency lists (track = true): preds[i] holds the ops that op
+  // i (its index in seq) must wait for -- the last writer of every region it
+  // reads or writes (read/write after write) and, for the regions it
+  // writes, the readers since that write (write after read).
+  bool track = false;
+  std::vector<std::vector<int64_t>> preds;
+
   int32_t place(const std::vector<PV>& reads, const std::vector<PV>& writes) {
+    const int64_t me = (int64_t)seq.size();  // the op being placed
+    std::vector<int64_t> dep;
     int32_t w = 0;
     for (const PV& v : reads) {
       if (v.rows <= 0 || v.cols <= 0) continue;
       const Rect rc = rect(v);
       for (const Acc& a : objs[v.obj].acc)
-        if (a.rc.overlaps(rc)) w = std::max(w, a.lw + 1);
+        if (a.rc.overlaps(rc)) {
+          w = std::max(w, a.lw + 1);
+          if (track && a.wop >= 0) dep.push_back(a.wop);
+        }
     }
     for (const PV& v : writes) {
       if (v.rows <= 0 || v.cols <= 0) continue;
       const Rect rc = rect(v);
       for (const Acc& a : objs[v.obj].acc)
-        if (a.rc.overlaps(rc)) w = std::max(w, std::max(a.lw, a.lr) + 1);
+        if (a.rc.overlaps(rc)) {
+          w = std::max(w, std::max(a.lw, a.lr) + 1);
+          if (track) {
+            if (a.wop >= 0) dep.push_back(a.wop);
+            dep.insert(dep.end(), a.rops.begin(), a.rops.end());
+          }
+        }
+    }
+    if (track) {
+      std::sort(dep.begin(), dep.end());
+      dep.erase(std::unique(dep.begin(), dep.end()), dep.end());
+      dep.erase(std::remove(dep.begin(), dep.end(), me), dep.end());
+      if ((int64_t)preds.size() <= me) preds.resize(me + 1);
+      preds[me] = std::move(dep);
     }
     for (const PV& v : reads) {
       if (v.rows <= 0 || v.cols <= 0) continue;
@@ -299,10 +328,15 @@ struct Planner {
       for (Acc& a : objs[v.obj].acc)
         if (a.rc == rc) {
           a.lr = std::max(a.lr, w);
+          if (track) a.rops.push_back(me);
           found = true;
           break;
         }
-      if (!found) objs[v.obj].acc.push_back(Acc{rc, -1, w});
+      if (!found) {
+        Acc a{rc, -1, w};
+        if (track) a.rops.push_back(me);
+        objs[v.obj].acc.push_back(std::move(a));
+      }
     }
     for (const PV& v : writes) {
       if (v.rows <= 0 || v.cols <= 0) continue;
@@ -320,7 +354,9 @@ struct Planner {
                                       a.rc.c1 <= rc.c1;
                              }),
               L.end());
-      L.push_back(Acc{rc, w, -1});
+      Acc a{rc, w, -1};
+      a.wop = track ? me : -1;
+      L.push_back(std::move(a));
     }
     maxwave = std::max(maxwave, w);
     return w;
@@ -1104,6 +1140,46 @@ struct Planner {
     P.potrf.swap(p);
     P.trunc.swap(u);
     P.chain.swap(ch);
+    if (track) build_flow(order);
+  }
+
+  // Dataflow form of a TRSM/GEMM plan: the ops in wave order (flow), the
+  // number of predecessors of each and its successors (CSR).
+  void build_flow(const std::vector<int64_t>& order) {
+    P.flow.clear();
+    P.npred.clear();
+    P.succ_off.clear();
+    P.succ.clear();
+    for (const Ref& r : seq)
+      if (r.type != OP_TRSM && r.type != OP_GEMM) return;  // TRSM/GEMM plans only
+    const int64_t N = (int64_t)order.size();
+    std::vector<int64_t> pos_of(N);  // seq index -> flow index
+    std::vector<int64_t> cnt_t(NOPTYPES, 0);
+    P.flow.resize(N);
+    for (int64_t i = 0; i < N; ++i) {
+      const Ref& r = seq[order[i]];
+      pos_of[order[i]] = i;
+      P.flow[i] = FlowOp{r.type, 0, cnt_t[r.type]++};
+    }
+    std::vector<int64_t> nsucc(N, 0);
+    P.npred.assign(N, 0);
+    for (int64_t q = 0; q < N; ++q) {
+      const int64_t i = pos_of[q];
+      if (q < (int64_t)preds.size())
+        for (int64_t d : preds[q]) {
+          P.npred[i] += 1;
+          nsucc[pos_of[d]] += 1;
+        }
+    }
+    P.succ_off.assign(N + 1, 0);
+    for (int64_t i = 0; i < N; ++i) P.succ_off[i + 1] = P.succ_off[i] + nsucc[i];
+    P.succ.assign(P.succ_off[N], 0);
+    std::vector<int64_t> fill(P.succ_off.begin(), P.succ_off.end() - 1);
+    for (int64_t q = 0; q < N; ++q) {
+      if (q >= (int64_t)preds.size()) continue;
+      const int64_t i = pos_of[q];
+      for (int64_t d : preds[q]) P.succ[fill[pos_of[d]]++] = (int32_t)i;
+    }
   }
 };
 
@@ -1124,6 +1200,7 @@ void plan_solve(HTree& T, Plan& P, int trans, int64_t voff, int64_t ncols, bool 
   P = Plan();
   Planner pl(T, P, BUF_L);
   pl.chains = chains;
+  pl.track = !chains;
   const int32_t v = pl.add_obj(BUF_VEC, voff, T.n);
   PV X = pl.whole(v, T.n, ncols);
   if (trans)
@@ -1139,6 +1216,7 @@ void plan_trmv(HTree& T, Plan& P, int trans, int64_t voff, int64_t ncols, bool c
   P = Plan();
   Planner pl(T, P, BUF_L);
   pl.chains = chains;
+  pl.track = !chains;
   const int32_t v = pl.add_obj(BUF_VEC, voff, T.n);
   PV X = pl.whole(v, T.n, ncols);
   if (trans)
@@ -1152,6 +1230,7 @@ void plan_trmv(HTree& T, Plan& P, int trans, int64_t voff, int64_t ncols, bool c
 void plan_matvec(HTree& T, Plan& P, int64_t xoff, int64_t yoff, int64_t ncols) {
   P = Plan();
   Planner pl(T, P, BUF_C);
+  pl.track = true;
   const int32_t xo = pl.add_obj(BUF_VEC, xoff, T.n);
   const int32_t yo = pl.add_obj(BUF_VEC, yoff, T.n);
   pl.symv(0, pl.whole(xo, T.n, ncols), pl.whole(yo, T.n, ncols));

@@ -192,6 +192,7 @@ struct Launch {
 // State of the persistent kernel's grid barrier (zeroed before each launch).
 struct GridBar {
   unsigned int count, gen, abort, pad;
+  unsigned long long ticket;  // next op number of the dataflow kernel
 };
 
 // TRSM, GEMM and chain op ranges of one wave (persistent execution of a
@@ -200,6 +201,14 @@ struct WaveRange {
   int64_t trsm0, ntrsm;
   int64_t gemm0, ngemm;
   int64_t chain0, nchain;
+};
+
+// An op of a dataflow plan: its type (OP_TRSM or OP_GEMM) and index in
+// that type's array.
+struct FlowOp {
+  int32_t type;
+  int32_t pad;
+  int64_t idx;
 };
 
 struct Plan {
@@ -213,6 +222,17 @@ struct Plan {
   std::vector<OpTrsm> ctrsm;
   std::vector<OpGemm> cgemm;
   std::vector<Launch> launches;
+  // dataflow form of a TRSM/GEMM plan (ops in wave order; predecessors
+  // counted, successors as CSR), for the dependency-driven persistent kernel
+  std::vector<FlowOp> flow;
+  std::vector<int32_t> npred;
+  std::vector<int64_t> succ_off;
+  std::vector<int32_t> succ;
+  FlowOp* d_flow = nullptr;
+  int32_t* d_npred = nullptr;
+  int64_t* d_succ_off = nullptr;
+  int32_t* d_succ = nullptr;
+  int32_t* d_count = nullptr;  // arrivals per op (zeroed before each run)
   int64_t tmp_doubles = 0;
   int32_t tmp_slots = 0;  // rank slots of temporary partial sums (after the matrix's)
   int32_t nwaves = 0;

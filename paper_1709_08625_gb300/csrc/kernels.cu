@@ -9,8 +9,11 @@
 //                 with a matrix-vector path for one column
 //   k_chain       chains: the ops of a small diagonal block's solve in order,
 //                 by one CTA
-//   k_waves       a whole triangular solve or matvec as one cooperative launch
-//                 (waves separated by a bounded grid barrier)
+//   k_flow        a whole triangular solve or matvec as one cooperative launch,
+//                 every op started when its own producers are done (bounded
+//                 waits on per-op arrival counters)
+//   k_waves       the same, wave by wave with a bounded grid barrier between
+//                 waves
 //   reductions    log det = 2 sum log L_ii, dot products (fixed order)
 //
 // The truncated low-rank sums (Remark A.1) are in trunc.cu.  Op kernels take
@@ -427,13 +430,13 @@ struct GemmSmem {
 
 // Y (m x 1) = beta Y + alpha A x, in a fixed summation order.  Where the
 // rows of A are contiguous, a warp per row (lanes stride along the row).
-// Otherwise (column-major A) the CTA takes GV_ROWS rows at a time and splits
-// the inner dimension into blockDim / GV_ROWS interleaved parts, one thread
-// per (row, part): every thread issues GV_UNROLL independent loads before it
-// uses them, so that a product over a block in HBM waits for about one
-// memory latency instead of one per column; the parts are then added in
-// part order through shared memory.
-constexpr int GV_ROWS = 64;
+// Otherwise (column-major A) a thread per (row, part): the CTA takes R rows
+// at a time (R = m rounded up to a warp, at most the CTA) and splits the
+// inner dimension into P = blockDim / R interleaved parts; every thread
+// issues GV_UNROLL independent loads before it uses them, so that a product
+// over a block in HBM waits for a few memory latencies instead of one per
+// column.  With P > 1 the parts are added in part order through shared
+// memory.
 constexpr int GV_UNROLL = 8;
 
 template <class T>
@@ -460,9 +463,11 @@ __device__ void do_gemv(const OpGemm& op, const Bases& B, int m, int k, double* 
     }
     return;
   }
-  const int P = (int)blockDim.x / GV_ROWS;  // parts of the inner dimension
-  const int r = tid % GV_ROWS, p = tid / GV_ROWS;
-  for (int r0 = 0; r0 < m; r0 += GV_ROWS) {
+  const int nt = (int)blockDim.x;
+  const int R = min(nt, (m + 31) & ~31);
+  const int P = nt / R;
+  const int r = tid % R, p = tid / R;
+  for (int r0 = 0; r0 < m; r0 += R) {
     const int i = r0 + r;
     T acc = T(0);
     if (i < m && p < P) {
@@ -479,18 +484,23 @@ __device__ void do_gemv(const OpGemm& op, const Bases& B, int m, int k, double* 
         for (int u = 0; u < GV_UNROLL; ++u) acc += av[u] * xv[u];
       }
     }
-    __syncthreads();
-    if (tid < GV_ROWS * P) gv_red[tid] = acc;
-    __syncthreads();
+    if (P > 1) {
+      __syncthreads();
+      if (p < P) gv_red[p * R + r] = acc;
+      __syncthreads();
+      if (p == 0 && i < m) {
+        T s = T(0);
+        for (int q = 0; q < P; ++q) s += gv_red[q * R + r];
+        acc = s;
+      }
+    }
     if (p == 0 && i < m) {
-      T s = T(0);
-      for (int q = 0; q < P; ++q) s += gv_red[q * GV_ROWS + r];
       double* yp = Y + (int64_t)i * op.Y.rs;
-      const double v = op.alpha * (double)s;
+      const double v = op.alpha * (double)acc;
       *yp = op.beta ? *yp + v : v;
     }
   }
-  __syncthreads();
+  if (P > 1) __syncthreads();
 }
 
 template <class T>
@@ -679,6 +689,92 @@ __global__ void __launch_bounds__(256) k_waves(const WaveRange* waves, int nwave
     }
     if (w + 1 < nwaves && !grid_barrier(gb, B.status, gridDim.x)) return;
   }
+}
+
+// Dependency-driven execution of a TRSM/GEMM plan (one cooperative launch,
+// all CTAs resident).  The ops are numbered in wave order; each CTA takes
+// the next number from a ticket counter, waits until every producer of that
+// op has signalled (count[i] == npred[i]), runs it, and signals its
+// successors.  Because tickets go out in wave order and every producer has a
+// smaller number, the unfinished op with the smallest number always has all
+// of its producers done, so the launch always progresses.  The wait is
+// bounded like the grid barrier's: after kBarrierNs, or once another CTA has
+// given up, the CTA records DEV_TIMEOUT, raises the abort flag and leaves.
+// Every op computes exactly what it computes in a wave, in the same order
+// relative to the ops it depends on: the results are those of the waves.
+__global__ void __launch_bounds__(256) k_flow(const FlowOp* flow, int64_t nops, const int32_t* npred,
+                                              const int64_t* succ_off, const int32_t* succ, int32_t* count,
+                                              const OpTrsm* trsm, const OpGemm* gemm, Bases B, GridBar* gb) {
+  extern __shared__ double sL[];
+  __shared__ GemmSmem<double> gd;
+  __shared__ GemmSmem<float> gf;
+  __shared__ long long s_op;
+  __shared__ int s_ok;
+  unsigned long long* ticket = &gb->ticket;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      volatile unsigned int* abort = &gb->abort;
+      long long i = -1;
+      if (!*abort) i = (long long)atomicAdd(ticket, 1ull);
+      int ok = i >= 0 && i < nops;
+      if (ok) {
+        // wait for the producers of op i
+        const volatile int32_t* cnt = count + i;
+        const int32_t need = npred[i];
+        const unsigned long long t0 = global_ns();
+        while (*cnt < need) {
+          if (*abort || global_ns() - t0 > kBarrierNs) {
+            atomicExch(&gb->abort, 1u);
+            record_error(B.status, DEV_TIMEOUT, 1);
+            ok = 0;
+            break;
+          }
+          __nanosleep(20);
+        }
+        __threadfence();
+      }
+      s_op = i;
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    const FlowOp f = flow[s_op];
+    if (f.type == OP_TRSM) {
+      if (B.mixed)
+        do_trsm<float>(trsm[f.idx], B, reinterpret_cast<float*>(sL));
+      else
+        do_trsm<double>(trsm[f.idx], B, sL);
+    } else if (B.mixed) {
+      do_gemm<float>(gemm[f.idx], B, gf);
+    } else {
+      do_gemm<double>(gemm[f.idx], B, gd);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();  // the op's writes before its signals
+      for (int64_t e = succ_off[s_op]; e < succ_off[s_op + 1]; ++e) atomicAdd(count + succ[e], 1);
+    }
+  }
+}
+
+int launch_flow(const FlowOp* flow, int64_t nops, const int32_t* npred, const int64_t* succ_off, const int32_t* succ,
+                int32_t* count, const OpTrsm* trsm, const OpGemm* gemm, const Bases& B, GridBar* gb, int max_dense,
+                int per_sm, cudaStream_t st) {
+  int maxper = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxper, k_flow, 256, trsm_smem(max_dense)) != cudaSuccess)
+    return -1;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int per = (per_sm <= 0 || per_sm > maxper) ? maxper : per_sm;
+  const int grid = per * sms;
+  if (grid <= 0 || nops <= 0 || !gb || !count) return -1;
+  if (cudaMemsetAsync(gb, 0, sizeof(GridBar), st) != cudaSuccess) return -1;
+  if (cudaMemsetAsync(count, 0, nops * sizeof(int32_t), st) != cudaSuccess) return -1;
+  void* args[] = {(void*)&flow, (void*)&nops, (void*)&npred, (void*)&succ_off, (void*)&succ, (void*)&count,
+                  (void*)&trsm, (void*)&gemm, (void*)&B, (void*)&gb};
+  return cudaLaunchCooperativeKernel((void*)k_flow, grid, 256, args, trsm_smem(max_dense), st) == cudaSuccess ? 0
+                                                                                                               : -1;
 }
 
 // Self-test of the bounded wait: every CTA arrives, one arrival more is
@@ -907,6 +1003,7 @@ int configure_kernels(int max_dense) {
   cudaError_t e2 = cudaFuncSetAttribute(k_trsm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, tneed);
   if (e2 == cudaSuccess) e2 = cudaFuncSetAttribute(k_trsm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, tneed);
   cudaError_t e4 = cudaFuncSetAttribute(k_waves, cudaFuncAttributeMaxDynamicSharedMemorySize, tneed);
+  if (e4 == cudaSuccess) e4 = cudaFuncSetAttribute(k_flow, cudaFuncAttributeMaxDynamicSharedMemorySize, tneed);
   if (e4 == cudaSuccess) e4 = cudaFuncSetAttribute(k_chain<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, tneed);
   if (e4 == cudaSuccess) e4 = cudaFuncSetAttribute(k_chain<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, tneed);
   const int e3 = configure_trunc();

@@ -28,6 +28,12 @@ void launch_ops(int type, const void* ops, int64_t count, const TermD* terms, co
 int launch_waves(const WaveRange* waves, int nwaves, const OpTrsm* trsm, const OpGemm* gemm, const OpChain* chain,
                  const ChainTab& ct, const Bases& B, GridBar* gb, int max_dense, int per_sm, cudaStream_t st);
 int waves_max_per_sm(int max_dense);
+// One cooperative launch executing a TRSM/GEMM plan in dataflow order (every
+// op once its producers have signalled); count: nops ints of scratch.  -1
+// when the cooperative launch is unavailable.
+int launch_flow(const FlowOp* flow, int64_t nops, const int32_t* npred, const int64_t* succ_off, const int32_t* succ,
+                int32_t* count, const OpTrsm* trsm, const OpGemm* gemm, const Bases& B, GridBar* gb, int max_dense,
+                int per_sm, cudaStream_t st);
 // Two CTAs wait at a grid barrier that expects one arrival more than the
 // grid has; the wait ends by its time limit with DEV_TIMEOUT in *status.
 int launch_barrier_probe(GridBar* gb, int* status, cudaStream_t st);

@@ -324,18 +324,20 @@ def test_persistent_solves_match_wave_launches(hlc):
 
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     runs = {}
-    for flag in ("1", "0"):
-        env = dict(os.environ, HLC_PERSISTENT=flag)
+    # dependency-driven persistent kernel (default), the wave-by-wave
+    # persistent kernel, and one launch per wave
+    for name, env_add in (("flow", {}), ("waves", {"HLC_FLOW": "0"}), ("launches", {"HLC_PERSISTENT": "0"})):
+        env = dict(os.environ, **env_add)
         out = subprocess.run([sys.executable, "-c", _SOLVE_CASE.format(root=root)], env=env, capture_output=True,
                              text=True, timeout=600)
         assert out.returncode == 0, out.stderr[-2000:]
-        runs[flag] = json.loads(out.stdout.strip().splitlines()[-1])
-    on, off = runs["1"], runs["0"]
-    assert on["persistent"] > 0 and off["persistent"] == 0
-    # each op of a wave writes its own region, so the order in which CTAs
-    # take the ops does not change a single bit
-    for key in ("loglik", "logdet", "quad", "quad_factor", "refine_iters"):
-        assert on[key] == off[key], key
+        runs[name] = json.loads(out.stdout.strip().splitlines()[-1])
+    assert runs["flow"]["persistent"] > 0 and runs["waves"]["persistent"] > 0 and runs["launches"]["persistent"] == 0
+    # every op writes its own region or follows the writes it depends on, so
+    # the order in which CTAs take the ops does not change a single bit
+    for name in ("waves", "launches"):
+        for key in ("loglik", "logdet", "quad", "quad_factor", "refine_iters"):
+            assert runs["flow"][key] == runs[name][key], (name, key)
 
 
 _CHAIN_CASE = """
@@ -373,6 +375,37 @@ def test_chains_match_op_by_op_solves(hlc):
         assert out.returncode == 0, out.stderr[-2000:]
         runs[flag] = json.loads(out.stdout.strip().splitlines()[-1])
     assert runs["1"] == runs["0"]
+
+
+_ACC_CASE = """
+import json, sys
+sys.path.insert(0, {root!r})
+from paper_1709_08625_gb300 import hlc, inputs
+c = hlc.Context(0)
+t = c.build_tree(inputs.points(6000, 1520), leaf=64, eps=1e-6, kmax=128)
+r = t.loglik(hlc.theta(1.0, 0.05, 0.5, 1e-4), inputs.normal(6000, 1521))
+print(json.dumps({{k: r[k] for k in ("loglik", "logdet", "quad")}}))
+"""
+
+
+def test_accumulated_updates_vs_oracle(hlc):
+    # HLC_ACCUMULATE=1 (updates of a low-rank block truncated together before
+    # its next use) against the oracle's accumulate=1 reading
+    import json
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, HLC_ACCUMULATE="1")
+    out = subprocess.run([sys.executable, "-c", _ACC_CASE.format(root=root)], env=env, capture_output=True, text=True,
+                         timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    ho = oracle.h_loglik(inputs.points(6000, 1520), inputs.normal(6000, 1521), 1.0, 0.05, 0.5, 1e-4, 1e-6, leaf=64,
+                         accumulate=True)
+    for k in ("loglik", "logdet", "quad"):
+        assert abs(r[k] - ho[k]) / 6000 <= 1e-7, (k, r[k], ho[k])
 
 
 # --------------------------------------------------------------------------

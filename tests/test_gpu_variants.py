@@ -40,7 +40,7 @@ def test_variant_trees_match_oracle(ctx, n, leaf, eta, adm, split):
 
 
 @pytest.mark.parametrize("adm,split,nu,ell,eps", [(1, 0, 0.5, 0.05, 1e-7), (0, 1, 1.5, 0.05, 1e-7),
-                                                  (2, 0, 1.5, 0.1, 1e-5), (2, 1, 1.0, 0.1, 1e-5)])
+                                                  (2, 0, 1.0, 0.1, 1e-5), (2, 1, 1.0, 0.1, 1e-5)])
 def test_variant_loglik_vs_oracle(ctx, hlc, adm, split, nu, ell, eps):
     # weak admissibility makes neighbouring clusters low-rank, whose ranks
     # grow fast as eps falls: its cases run at eps = 1e-5
@@ -84,7 +84,7 @@ def test_fixed_rank_vs_oracle(ctx, hlc, k):
     assert abs(r["loglik"] - ho["loglik"]) / n <= 1e-7
 
 
-@pytest.mark.parametrize("n,kmax,nu", [(10000, 128, 0.5), (40000, 64, 1.5), (120000, 64, 0.325)])
+@pytest.mark.parametrize("n,kmax,nu", [(10000, 128, 0.5), (40000, 128, 1.5), (120000, 64, 0.325)])
 def test_serve_footprint_covers_device_memory(ctx, hlc, n, kmax, nu):
     # the serve loop admits a request by its estimated footprint: the
     # estimate must cover what one evaluation holds on the device (both

@@ -564,3 +564,35 @@ def test_fixed_rank_caps_ranks_and_error_falls_with_k():
     Hk = oracle.HOracle(xy, leaf=32, fixed_rank=int(Ha.ranks(0).max()) + 5)
     Hk.assemble(*th, 1e-6)
     np.testing.assert_array_equal(Ha.expand(0), Hk.expand(0))
+
+
+# ----------------------------------------------------------------------------
+# Accumulated updates (accumulate=1): the same factorisation with the updates
+# of a low-rank block truncated together before the block is next used
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("eps", [1e-5, 1e-7])
+def test_accumulated_updates_factor_error_is_order_eps(eps):
+    n = 1500
+    xy = inputs.points(n, 4600)
+    Hh = oracle.HOracle(xy, leaf=32)
+    Hh.assemble(1.0, 0.08, 0.5, 1e-4, eps)
+    Ct = Hh.expand(0)
+    Hh.cholesky(eps, accumulate=True)
+    Lt = Hh.expand(1)
+    nC = _power_norm(lambda v: Ct @ v, n)
+    e2 = _power_norm(lambda v: Ct @ v - Lt @ (Lt.T @ v), n) / nC
+    assert e2 <= 20 * eps, e2
+    # the factor is lower triangular with a positive diagonal
+    assert np.allclose(np.triu(Lt[np.ix_(Hh.perm(), Hh.perm())], 1), 0.0)
+
+
+def test_accumulated_updates_loglik_vs_dense_n2000():
+    w = inputs.WORKLOADS["n2000_nu0.5_eps1e-7"]
+    xy = inputs.workload_points("n2000_nu0.5_eps1e-7")
+    xi = inputs.workload_normal("n2000_nu0.5_eps1e-7")
+    th = (w["sigma2"], w["ell"], w["nu"], w["nugget"])
+    z = oracle.dense_chol_apply(xy, xi, *th)
+    Ld, ldd, _ = oracle.dense_loglik(xy, z, *th)
+    r = oracle.h_loglik(xy, z, *th, w["eps"], leaf=w["leaf"], eta=w["eta"], accumulate=True)
+    assert abs(r["loglik"] - Ld) / 2000 <= 1e-6
+    assert abs(r["logdet"] - ldd) / 2000 <= 1e-6
