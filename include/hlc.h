@@ -39,6 +39,9 @@
  *                     truncated at once)
  *   HLC_PERSISTENT=0  run triangular solves and matvecs wave by wave instead of
  *                     as one cooperative launch
+ *   HLC_FACTOR_FLOW=0 replay the H-Cholesky's waves from a CUDA graph instead of
+ *                     running it as one dependency-driven cooperative launch
+ *                     (same result, bit for bit)
  *   HLC_FLOW=0        in that cooperative launch, separate the waves by a grid
  *                     barrier instead of starting every op once its own
  *                     producers are done (same result, bit for bit)

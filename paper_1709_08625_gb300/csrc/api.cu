@@ -175,6 +175,7 @@ int upload_plan(Plan& P) {
   if ((st = upload(&P.d_succ_off, P.succ_off))) return st;
   if ((st = upload(&P.d_succ, P.succ))) return st;
   if (!P.flow.empty()) CK(cudaMalloc(&P.d_count, P.flow.size() * sizeof(int32_t)));
+  if (P.ngroups > 0) CK(cudaMalloc(&P.d_groups, P.ngroups * sizeof(TrGroup)));
   if ((st = upload(&P.d_chain, P.chain))) return st;
   if ((st = upload(&P.d_citems, P.citems))) return st;
   if ((st = upload(&P.d_ctrsm, P.ctrsm))) return st;
@@ -197,6 +198,8 @@ void free_plan(Plan& P) {
   cudaFree(P.d_succ_off);
   cudaFree(P.d_succ);
   cudaFree(P.d_count);
+  cudaFree(P.d_groups);
+  P.d_groups = nullptr;
   P.d_flow = nullptr;
   P.d_npred = nullptr;
   P.d_succ_off = nullptr;
@@ -275,6 +278,13 @@ constexpr int kTuneCandidates[3] = {1, 2, 4};
 // evaluation at n = 524,288)
 bool chains_enabled() {
   static const bool on = getenv("HLC_CHAINS") && getenv("HLC_CHAINS")[0] == '1';
+  return on;
+}
+
+// The factorisation runs as one dependency-driven launch (k_factor) unless
+// HLC_FACTOR_FLOW=0, which replays its waves from a CUDA graph
+bool factor_flow_enabled() {
+  static const bool on = !(getenv("HLC_FACTOR_FLOW") && getenv("HLC_FACTOR_FLOW")[0] == '0');
   return on;
 }
 
@@ -583,7 +593,7 @@ int build_plans(hlc_tree* t, bool chol, bool solve) {
   try {
     if (chol && !t->chol_ready) {
       const bool acc = getenv("HLC_ACCUMULATE") && getenv("HLC_ACCUMULATE")[0] == '1';
-      plan_cholesky(t->T, t->chol, acc);
+      plan_cholesky(t->T, t->chol, acc, factor_flow_enabled());
       int st = check_plan(t, t->chol);
       if (st) return st;
       st = upload_plan(t->chol);
@@ -693,7 +703,20 @@ int do_cholesky(hlc_tree* t, const hlc_hmat* C, hlc_hmat* L) {
   if (t->T.nslots)
     CK(cudaMemcpyAsync(L->ranks, C->ranks, t->T.nslots * sizeof(int), cudaMemcpyDeviceToDevice, c->stream));
   Bases B = make_bases(t, L->arena, nullptr, L->ranks, t->p.precision != HLC_FP64);
-  run_plan(t, t->chol, B, c->stream);
+  // one dependency-driven launch (serve slots share the SMs and take the
+  // waves; so do the timed profiling passes, which time launches by type)
+  bool flowed = false;
+  if (factor_flow_enabled() && c->persistent && !c->profiling && !g_prof.on && t->chol.d_flow) {
+    const int md = (int)std::max<int64_t>(t->T.max_dense_dim, t->T.leaf);
+    if (launch_factor(t->chol, B, c->d_gridbar, md, c->stream) == 0) {
+      flowed = true;
+      c->launches += 1;
+      c->persistent_launches += 1;
+    } else {
+      cudaGetLastError();
+    }
+  }
+  if (!flowed) run_plan(t, t->chol, B, c->stream);
   CK(cudaGetLastError());
   L->valid = false;
   st = take_status(c);

@@ -90,4 +90,53 @@ __device__ __forceinline__ int block_argmax(double v, int idx, double* redv, int
   return redi[32];
 }
 
+// Bounded waits: a CTA gives up after kBarrierNs (or once another CTA has
+// given up), records DEV_TIMEOUT, raises the abort flag and leaves.
+constexpr unsigned long long kBarrierNs = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Barrier of `expected` CTAs in global memory.  Thread 0 of each CTA
+// arrives on *count; the last to arrive resets it and advances *gen, which
+// the others wait on.  Returns false when the wait gave up (time limit, or
+// the abort flag raised by another CTA); the caller then leaves.
+__device__ __forceinline__ bool bounded_barrier(unsigned int* count, unsigned int* gen_p, unsigned int expected,
+                                                unsigned int* abort_p, int* status) {
+  __shared__ int bb_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* gen = gen_p;
+    volatile unsigned int* abort = abort_p;
+    int good = *abort == 0;
+    if (good) {
+      const unsigned int g = *gen;
+      __threadfence();
+      if (atomicAdd(count, 1u) == expected - 1) {
+        atomicExch(count, 0u);
+        __threadfence();
+        atomicAdd(gen_p, 1u);
+      } else {
+        const unsigned long long t0 = global_ns();
+        while (*gen == g) {
+          if (*abort || global_ns() - t0 > kBarrierNs) {
+            atomicExch(abort_p, 1u);
+            record_error(status, DEV_TIMEOUT, 0);
+            good = 0;
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+      __threadfence();
+    }
+    bb_ok = good;
+  }
+  __syncthreads();
+  return bb_ok != 0;
+}
+
 }  // namespace hlc

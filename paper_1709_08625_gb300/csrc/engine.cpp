@@ -1143,52 +1143,61 @@ struct Planner {
     if (track) build_flow(order);
   }
 
-  // Dataflow form of a TRSM/GEMM plan: the ops in wave order (flow), the
-  // number of predecessors of each and its successors (CSR).
+  // Dataflow form of a plan: the ops in wave order (flow), the number of
+  // predecessors of each and its successors (CSR).  A group truncation
+  // (OP_TRUNC_BIG) becomes kGroupParts consecutive entries: every part waits
+  // for the op's producers, and part 0 alone signals the op's consumers
+  // (after the group's last barrier, when every part is done).
+  static constexpr int kGroupParts = 8;
   void build_flow(const std::vector<int64_t>& order) {
     P.flow.clear();
     P.npred.clear();
     P.succ_off.clear();
     P.succ.clear();
-    for (const Ref& r : seq)
-      if (r.type != OP_TRSM && r.type != OP_GEMM) return;  // TRSM/GEMM plans only
+    P.ngroups = 0;
     const int64_t N = (int64_t)order.size();
-    std::vector<int64_t> pos_of(N);  // seq index -> flow index
+    std::vector<int64_t> pos_of(N), parts_of(N);  // seq index -> first flow index, parts
     std::vector<int64_t> cnt_t(NOPTYPES, 0);
-    P.flow.resize(N);
     for (int64_t i = 0; i < N; ++i) {
       const Ref& r = seq[order[i]];
-      pos_of[order[i]] = i;
-      P.flow[i] = FlowOp{r.type, 0, cnt_t[r.type]++};
+      pos_of[order[i]] = (int64_t)P.flow.size();
+      const int np = r.type == OP_TRUNC_BIG ? kGroupParts : 1;
+      parts_of[order[i]] = np;
+      const int32_t arr = r.type == OP_TRUNC_BIG ? OP_TRUNC : r.type;  // both truncation kinds share one array
+      const int64_t idx = cnt_t[arr]++;
+      const int64_t grp = np > 1 ? P.ngroups++ : -1;
+      for (int p = 0; p < np; ++p) P.flow.push_back(FlowOp{r.type, p, idx, grp});
     }
-    std::vector<int64_t> nsucc(N, 0);
-    P.npred.assign(N, 0);
+    const int64_t F = (int64_t)P.flow.size();
+    std::vector<int64_t> nsucc(F, 0);
+    P.npred.assign(F, 0);
     for (int64_t q = 0; q < N; ++q) {
-      const int64_t i = pos_of[q];
-      if (q < (int64_t)preds.size())
-        for (int64_t d : preds[q]) {
-          P.npred[i] += 1;
+      if (q >= (int64_t)preds.size()) continue;
+      for (int64_t d : preds[q])
+        for (int64_t p = 0; p < parts_of[q]; ++p) {
+          P.npred[pos_of[q] + p] += 1;
           nsucc[pos_of[d]] += 1;
         }
     }
-    P.succ_off.assign(N + 1, 0);
-    for (int64_t i = 0; i < N; ++i) P.succ_off[i + 1] = P.succ_off[i] + nsucc[i];
-    P.succ.assign(P.succ_off[N], 0);
+    P.succ_off.assign(F + 1, 0);
+    for (int64_t i = 0; i < F; ++i) P.succ_off[i + 1] = P.succ_off[i] + nsucc[i];
+    P.succ.assign(P.succ_off[F], 0);
     std::vector<int64_t> fill(P.succ_off.begin(), P.succ_off.end() - 1);
     for (int64_t q = 0; q < N; ++q) {
       if (q >= (int64_t)preds.size()) continue;
-      const int64_t i = pos_of[q];
-      for (int64_t d : preds[q]) P.succ[fill[pos_of[d]]++] = (int32_t)i;
+      for (int64_t d : preds[q])
+        for (int64_t p = 0; p < parts_of[q]; ++p) P.succ[fill[pos_of[d]]++] = (int32_t)(pos_of[q] + p);
     }
   }
 };
 
 }  // namespace
 
-void plan_cholesky(HTree& T, Plan& P, bool accumulate) {
+void plan_cholesky(HTree& T, Plan& P, bool accumulate, bool flow) {
   P = Plan();
   Planner pl(T, P, BUF_L);
   pl.defer = accumulate;
+  pl.track = flow;
   pl.chol(0);
   pl.flush_all();
   pl.finish();

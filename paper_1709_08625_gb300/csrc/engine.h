@@ -32,7 +32,9 @@ void layout(HTree& T, int kmax);
 
 // accumulate: updates of a low-rank block are truncated together right before
 // the block is next used (accumulated updates) instead of one at a time.
-void plan_cholesky(HTree& T, Plan& P, bool accumulate = false);
+// flow: also build the plan's dataflow form (op-level dependencies) for the
+// dependency-driven factorisation kernel
+void plan_cholesky(HTree& T, Plan& P, bool accumulate = false, bool flow = false);
 // chains: the solve of every subdivided diagonal block of at most 1024 rows
 // becomes one op (a chain run by one CTA)
 void plan_solve(HTree& T, Plan& P, int trans, int64_t voff, int64_t ncols, bool chains = false);

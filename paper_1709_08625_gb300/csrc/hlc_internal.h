@@ -203,12 +203,22 @@ struct WaveRange {
   int64_t chain0, nchain;
 };
 
-// An op of a dataflow plan: its type (OP_TRSM or OP_GEMM) and index in
-// that type's array.
+// An op of a dataflow plan: its type and index in that type's array.  A
+// truncation run by a group of CTAs (OP_TRUNC_BIG) has one entry per part
+// (part 0..parts-1, consecutive), sharing the group record `group`.
 struct FlowOp {
   int32_t type;
-  int32_t pad;
+  int32_t part;
   int64_t idx;
+  int64_t group;
+};
+
+// Rendezvous of the CTAs that run the parts of one group truncation in the
+// dataflow factorisation (zeroed before each run): a bounded barrier and the
+// CTA of every part (whose scratch slice the others read).
+struct TrGroup {
+  unsigned int count, gen;
+  int32_t cta[8];
 };
 
 struct Plan {
@@ -233,6 +243,8 @@ struct Plan {
   int64_t* d_succ_off = nullptr;
   int32_t* d_succ = nullptr;
   int32_t* d_count = nullptr;  // arrivals per op (zeroed before each run)
+  int64_t ngroups = 0;         // group truncations (OP_TRUNC_BIG) of a dataflow factorisation
+  TrGroup* d_groups = nullptr;
   int64_t tmp_doubles = 0;
   int32_t tmp_slots = 0;  // rank slots of temporary partial sums (after the matrix's)
   int32_t nwaves = 0;

@@ -42,6 +42,7 @@
 #include "devutil.cuh"
 #include "hlc_internal.h"
 #include "kernels.h"
+#include "ops.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -769,15 +770,21 @@ __device__ int tr_batch(const OpTrunc& op, const TermD* tl, const int* ranks, in
   return kacc + kb;
 }
 
+// Shared-memory state of one CTA running truncation ops.
+template <class C>
+struct TrShared {
+  TrCat cat;
+  CoreShared<C> cs;
+  double sh[2];
+};
+
+// One truncation op by one CTA (scr: the CTA's scratch slice).
 template <class T, class C>
-__global__ void __launch_bounds__(TR_THREADS, sizeof(T) == 4 ? 2 : 1) k_trunc(const OpTrunc* ops, int64_t count, const TermD* terms,
-                                                       Bases B) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  T* sC = reinterpret_cast<T*>(smraw);
-  __shared__ TrCat cat;
-  __shared__ CoreShared<C> cs;
-  __shared__ double sh[2];
-  double* scr = B.scratch + (int64_t)blockIdx.x * TR_SCRATCH;
+__device__ void trunc_one(const OpTrunc& op, const TermD* terms, const Bases& B, double* scr, T* sC,
+                          TrShared<C>& ts) {
+  TrCat& cat = ts.cat;
+  CoreShared<C>& cs = ts.cs;
+  double* sh = ts.sh;
   T* Pu = reinterpret_cast<T*>(scr);
   T* Pv = reinterpret_cast<T*>(scr + TR_REG);
   C* M = reinterpret_cast<C*>(scr + 2 * TR_REG);
@@ -786,72 +793,77 @@ __global__ void __launch_bounds__(TR_THREADS, sizeof(T) == 4 ? 2 : 1) k_trunc(co
   C* X = reinterpret_cast<C*>(scr + TR_OFF_X);
   C* Cu = reinterpret_cast<C*>(scr + TR_OFF_CU);
   C* Cv = reinterpret_cast<C*>(scr + TR_OFF_CV);
-  for (int64_t o = blockIdx.x; o < count; o += gridDim.x) {
-    const OpTrunc op = ops[o];
-    const TermD* tl = terms + op.term0;
-    int kacc = op.keep ? B.ranks[op.slot] : 0;
-    int t0 = 0;
-    bool first = true;
-    while (first || t0 < op.nterms) {
-      first = false;
-      int t1;
-      const int K = tr_batch(op, tl, B.ranks, kacc, t0, &t1, cat);
-      t0 = t1;
-      if (K == 0) {
-        kacc = 0;
-        continue;
-      }
-      if (K > TR_KT) {
-        if (threadIdx.x == 0) record_error(B.status, DEV_RANK, K);
-        kacc = 0;
-        break;
-      }
-      long long tp = clock64();
-      if (B.phase && threadIdx.x == 0) {
-        atomicAdd(B.phase + 11, 1ull);
-        atomicAdd(B.phase + 12, (unsigned long long)K);
-      }
-      if (K <= 32) {
-        qr_tsqr_pair<T>([&](int r, int c) { return cat_value(B, op, cat, 0, r, c); }, op.m,
-                        [&](int r, int c) { return cat_value(B, op, cat, 1, r, c); }, op.n, K, Pu, Pv, sC);
-        phase_mark(B.phase, 1, tp);
-      } else {
-        qr_stream<T>([&](int r, int c) { return cat_value(B, op, cat, 0, r, c); }, op.m, K, Pu, sC, sh);
-        phase_mark(B.phase, 1, tp);
-        qr_stream<T>([&](int r, int c) { return cat_value(B, op, cat, 1, r, c); }, op.n, K, Pv, sC, sh);
-      }
-      phase_mark(B.phase, 2, tp);
-      tr_core<T, C>(Pu, Pv, K, op.eps, op.kcap, op.kfix, M, W, J, X, Cu, Cv, cs, B.status, B.phase);
-      tp = clock64();
-      const int k = cs.k;
-      // algorithmic flops of the batch: two streamed R factors and the apply
-      if (B.flops && threadIdx.x == 0)
-        atomicAdd(B.flops + OP_TRUNC, 2.0 * K * K * (double)(op.m + op.n) + 2.0 * K * (double)k * (op.m + op.n));
-      tr_apply<T, C>(B, op, cat, 0, 0, op.m, K, k, Cu, sC);
-      tr_apply<T, C>(B, op, cat, 1, 0, op.n, K, k, Cv, sC);
-      phase_mark(B.phase, 7, tp);
-      kacc = k;
-      __syncthreads();
+  const TermD* tl = terms + op.term0;
+  int kacc = op.keep ? B.ranks[op.slot] : 0;
+  int t0 = 0;
+  bool first = true;
+  while (first || t0 < op.nterms) {
+    first = false;
+    int t1;
+    const int K = tr_batch(op, tl, B.ranks, kacc, t0, &t1, cat);
+    t0 = t1;
+    if (K == 0) {
+      kacc = 0;
+      continue;
     }
-    if (threadIdx.x == 0) B.ranks[op.slot] = kacc;
+    if (K > TR_KT) {
+      if (threadIdx.x == 0) record_error(B.status, DEV_RANK, K);
+      kacc = 0;
+      break;
+    }
+    long long tp = clock64();
+    if (B.phase && threadIdx.x == 0) {
+      atomicAdd(B.phase + 11, 1ull);
+      atomicAdd(B.phase + 12, (unsigned long long)K);
+    }
+    if (K <= 32) {
+      qr_tsqr_pair<T>([&](int r, int c) { return cat_value(B, op, cat, 0, r, c); }, op.m,
+                      [&](int r, int c) { return cat_value(B, op, cat, 1, r, c); }, op.n, K, Pu, Pv, sC);
+      phase_mark(B.phase, 1, tp);
+    } else {
+      qr_stream<T>([&](int r, int c) { return cat_value(B, op, cat, 0, r, c); }, op.m, K, Pu, sC, sh);
+      phase_mark(B.phase, 1, tp);
+      qr_stream<T>([&](int r, int c) { return cat_value(B, op, cat, 1, r, c); }, op.n, K, Pv, sC, sh);
+    }
+    phase_mark(B.phase, 2, tp);
+    tr_core<T, C>(Pu, Pv, K, op.eps, op.kcap, op.kfix, M, W, J, X, Cu, Cv, cs, B.status, B.phase);
+    tp = clock64();
+    const int k = cs.k;
+    // algorithmic flops of the batch: two streamed R factors and the apply
+    if (B.flops && threadIdx.x == 0)
+      atomicAdd(B.flops + OP_TRUNC, 2.0 * K * K * (double)(op.m + op.n) + 2.0 * K * (double)k * (op.m + op.n));
+    tr_apply<T, C>(B, op, cat, 0, 0, op.m, K, k, Cu, sC);
+    tr_apply<T, C>(B, op, cat, 1, 0, op.n, K, k, Cv, sC);
+    phase_mark(B.phase, 7, tp);
+    kacc = k;
     __syncthreads();
   }
+  if (threadIdx.x == 0) B.ranks[op.slot] = kacc;
+  __syncthreads();
 }
 
-// Cluster variant for large targets: the TR_CL CTAs of a cluster share one op.
 template <class T, class C>
-__global__ void __cluster_dims__(TR_CL, 1, 1) __launch_bounds__(TR_THREADS, sizeof(T) == 4 ? 2 : 1)
-    k_trunc_cl(const OpTrunc* ops, int64_t count, const TermD* terms, Bases B) {
+__global__ void __launch_bounds__(TR_THREADS, sizeof(T) == 4 ? 2 : 1) k_trunc(const OpTrunc* ops, int64_t count, const TermD* terms,
+                                                       Bases B) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* sC = reinterpret_cast<T*>(smraw);
-  __shared__ TrCat cat;
-  __shared__ CoreShared<C> cs;
-  __shared__ double sh[2];
-  cg::cluster_group cluster = cg::this_cluster();
-  const int rk = (int)cluster.block_rank();
-  const int64_t cid = blockIdx.x / TR_CL, ncl = gridDim.x / TR_CL;
-  const int64_t base_cta = cid * TR_CL;  // first CTA of this cluster
-  auto scr_of = [&](int r) { return B.scratch + (base_cta + r) * TR_SCRATCH; };
+  __shared__ TrShared<C> ts;
+  double* scr = B.scratch + (int64_t)blockIdx.x * TR_SCRATCH;
+  for (int64_t o = blockIdx.x; o < count; o += gridDim.x)
+    trunc_one<T, C>(ops[o], terms, B, scr, reinterpret_cast<T*>(smraw), ts);
+}
+
+// One part (rk of TR_CL) of a truncation op shared by TR_CL CTAs: each
+// streams its share of the rows, parts 0 and 1 combine the partial R
+// factors, part 0 computes the core, all apply.  scr_of(r) is part r's
+// scratch slice; sync() separates the phases (a cluster barrier, or a
+// bounded barrier in global memory: false when it gave up, and then the part
+// stops).
+template <class T, class C, class ScrOf, class Sync>
+__device__ void trunc_part(const OpTrunc& op, const TermD* terms, const Bases& B, int rk, ScrOf scr_of, Sync sync,
+                           T* sC, TrShared<C>& ts) {
+  TrCat& cat = ts.cat;
+  CoreShared<C>& cs = ts.cs;
+  double* sh = ts.sh;
   double* scr = scr_of(rk);
   T* Pu = reinterpret_cast<T*>(scr);
   T* Pv = reinterpret_cast<T*>(scr + TR_REG);
@@ -859,90 +871,199 @@ __global__ void __cluster_dims__(TR_CL, 1, 1) __launch_bounds__(TR_THREADS, size
   C* W = reinterpret_cast<C*>(scr + 3 * TR_REG);
   C* J = reinterpret_cast<C*>(scr + 4 * TR_REG);
   C* X = reinterpret_cast<C*>(scr + TR_OFF_X);
-  C* Cu0 = reinterpret_cast<C*>(scr_of(0) + TR_OFF_CU);  // coefficients live with CTA 0
+  C* Cu0 = reinterpret_cast<C*>(scr_of(0) + TR_OFF_CU);  // coefficients live with part 0
   C* Cv0 = reinterpret_cast<C*>(scr_of(0) + TR_OFF_CV);
   int* flag0 = reinterpret_cast<int*>(scr_of(0) + TR_OFF_FLAG);
-  for (int64_t o = cid; o < count; o += ncl) {
-    const OpTrunc op = ops[o];
-    const TermD* tl = terms + op.term0;
-    int kacc = op.keep ? B.ranks[op.slot] : 0;
-    int t0 = 0;
-    bool first = true;
-    while (first || t0 < op.nterms) {
-      first = false;
-      int t1;
-      const int K = tr_batch(op, tl, B.ranks, kacc, t0, &t1, cat);
-      t0 = t1;
-      if (K == 0) {
-        kacc = 0;
-        continue;
-      }
-      if (K > TR_KT) {
-        if (threadIdx.x == 0 && rk == 0) record_error(B.status, DEV_RANK, K);
-        kacc = 0;
-        break;
-      }
-      const int mu0 = (int)((int64_t)op.m * rk / TR_CL), mu1 = (int)((int64_t)op.m * (rk + 1) / TR_CL);
-      const int nv0 = (int)((int64_t)op.n * rk / TR_CL), nv1 = (int)((int64_t)op.n * (rk + 1) / TR_CL);
-      // 1. partial R factors of this CTA's rows
-      if (K <= 32) {
-        qr_tsqr<T>([&](int r, int c) { return cat_value(B, op, cat, 0, mu0 + r, c); }, mu1 - mu0, K, Pu, sC);
-        qr_tsqr<T>([&](int r, int c) { return cat_value(B, op, cat, 1, nv0 + r, c); }, nv1 - nv0, K, Pv, sC);
-      } else {
-        qr_stream<T>([&](int r, int c) { return cat_value(B, op, cat, 0, mu0 + r, c); }, mu1 - mu0, K, Pu, sC, sh);
-        qr_stream<T>([&](int r, int c) { return cat_value(B, op, cat, 1, nv0 + r, c); }, nv1 - nv0, K, Pv, sC, sh);
-      }
-      __threadfence();
-      cluster.sync();
-      // 2. CTA 0 combines the U partials into its J region, CTA 1 the V partials
-      if (rk < 2) {
-        const int64_t poff = rk == 0 ? 0 : TR_REG;
-        T* fin = reinterpret_cast<T*>(J);
-        auto part = [&](int r, int c) {
-          const T* P = reinterpret_cast<const T*>(scr_of(r / K) + poff);
-          const int i = r % K;
-          return i <= c ? (double)P[i + (int64_t)c * TR_KT] : 0.0;
-        };
-        if (K <= 32)
-          qr_tsqr<T>(part, TR_CL * K, K, fin, sC);
-        else
-          qr_stream<T>(part, TR_CL * K, K, fin, sC, sh);
-      }
-      __threadfence();
-      cluster.sync();
-      // 3. CTA 0: core from R_u (own J) and R_v (CTA 1's J)
-      if (rk == 0) {
-        T* Ru = Pu;
-        T* Rv = Pv;
-        const T* fu = reinterpret_cast<const T*>(J);
-        const T* fv = reinterpret_cast<const T*>(scr_of(1) + 4 * TR_REG);
-        for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
-          const int i = e % K, j = e / K;
-          Ru[i + (int64_t)j * TR_KT] = fu[i + (int64_t)j * TR_KT];
-          Rv[i + (int64_t)j * TR_KT] = fv[i + (int64_t)j * TR_KT];
-        }
-        __syncthreads();
-        tr_core<T, C>(Ru, Rv, K, op.eps, op.kcap, op.kfix, M, W, J, X, Cu0, Cv0, cs, B.status);
-        if (threadIdx.x == 0) flag0[0] = cs.k;
-      }
-      __threadfence();
-      cluster.sync();
-      const int k = reinterpret_cast<const volatile int*>(flag0)[0];
-      if (B.flops && threadIdx.x == 0 && rk == 0)
-        atomicAdd(B.flops + OP_TRUNC_BIG,
-                  2.0 * K * K * (double)(op.m + op.n) + 2.0 * K * (double)k * (op.m + op.n));
-      // 4. all CTAs apply to their rows
-      tr_apply<T, C>(B, op, cat, 0, mu0, mu1, K, k, Cu0, sC);
-      tr_apply<T, C>(B, op, cat, 1, nv0, nv1, K, k, Cv0, sC);
-      kacc = k;
-      __threadfence();
-      cluster.sync();
+  const TermD* tl = terms + op.term0;
+  int kacc = op.keep ? B.ranks[op.slot] : 0;
+  int t0 = 0;
+  bool first = true;
+  while (first || t0 < op.nterms) {
+    first = false;
+    int t1;
+    const int K = tr_batch(op, tl, B.ranks, kacc, t0, &t1, cat);
+    t0 = t1;
+    if (K == 0) {
+      kacc = 0;
+      continue;
     }
-    if (threadIdx.x == 0 && rk == 0) B.ranks[op.slot] = kacc;
+    if (K > TR_KT) {
+      if (threadIdx.x == 0 && rk == 0) record_error(B.status, DEV_RANK, K);
+      kacc = 0;
+      break;
+    }
+    const int mu0 = (int)((int64_t)op.m * rk / TR_CL), mu1 = (int)((int64_t)op.m * (rk + 1) / TR_CL);
+    const int nv0 = (int)((int64_t)op.n * rk / TR_CL), nv1 = (int)((int64_t)op.n * (rk + 1) / TR_CL);
+    // 1. partial R factors of this part's rows
+    if (K <= 32) {
+      qr_tsqr<T>([&](int r, int c) { return cat_value(B, op, cat, 0, mu0 + r, c); }, mu1 - mu0, K, Pu, sC);
+      qr_tsqr<T>([&](int r, int c) { return cat_value(B, op, cat, 1, nv0 + r, c); }, nv1 - nv0, K, Pv, sC);
+    } else {
+      qr_stream<T>([&](int r, int c) { return cat_value(B, op, cat, 0, mu0 + r, c); }, mu1 - mu0, K, Pu, sC, sh);
+      qr_stream<T>([&](int r, int c) { return cat_value(B, op, cat, 1, nv0 + r, c); }, nv1 - nv0, K, Pv, sC, sh);
+    }
+    if (!sync()) return;
+    // 2. part 0 combines the U partials into its J region, part 1 the V partials
+    if (rk < 2) {
+      const int64_t poff = rk == 0 ? 0 : TR_REG;
+      T* fin = reinterpret_cast<T*>(J);
+      auto part = [&](int r, int c) {
+        const T* P = reinterpret_cast<const T*>(scr_of(r / K) + poff);
+        const int i = r % K;
+        return i <= c ? (double)P[i + (int64_t)c * TR_KT] : 0.0;
+      };
+      if (K <= 32)
+        qr_tsqr<T>(part, TR_CL * K, K, fin, sC);
+      else
+        qr_stream<T>(part, TR_CL * K, K, fin, sC, sh);
+    }
+    if (!sync()) return;
+    // 3. part 0: core from R_u (own J) and R_v (part 1's J)
+    if (rk == 0) {
+      T* Ru = Pu;
+      T* Rv = Pv;
+      const T* fu = reinterpret_cast<const T*>(J);
+      const T* fv = reinterpret_cast<const T*>(scr_of(1) + 4 * TR_REG);
+      for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+        const int i = e % K, j = e / K;
+        Ru[i + (int64_t)j * TR_KT] = fu[i + (int64_t)j * TR_KT];
+        Rv[i + (int64_t)j * TR_KT] = fv[i + (int64_t)j * TR_KT];
+      }
+      __syncthreads();
+      tr_core<T, C>(Ru, Rv, K, op.eps, op.kcap, op.kfix, M, W, J, X, Cu0, Cv0, cs, B.status);
+      if (threadIdx.x == 0) flag0[0] = cs.k;
+    }
+    if (!sync()) return;
+    const int k = reinterpret_cast<const volatile int*>(flag0)[0];
+    if (B.flops && threadIdx.x == 0 && rk == 0)
+      atomicAdd(B.flops + OP_TRUNC_BIG,
+                2.0 * K * K * (double)(op.m + op.n) + 2.0 * K * (double)k * (op.m + op.n));
+    // 4. all parts apply to their rows
+    tr_apply<T, C>(B, op, cat, 0, mu0, mu1, K, k, Cu0, sC);
+    tr_apply<T, C>(B, op, cat, 1, nv0, nv1, K, k, Cv0, sC);
+    kacc = k;
+    if (!sync()) return;
+  }
+  if (threadIdx.x == 0 && rk == 0) B.ranks[op.slot] = kacc;
+}
+
+// Cluster variant for large targets: the TR_CL CTAs of a cluster share one op.
+template <class T, class C>
+__global__ void __cluster_dims__(TR_CL, 1, 1) __launch_bounds__(TR_THREADS, sizeof(T) == 4 ? 2 : 1)
+    k_trunc_cl(const OpTrunc* ops, int64_t count, const TermD* terms, Bases B) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ TrShared<C> ts;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rk = (int)cluster.block_rank();
+  const int64_t cid = blockIdx.x / TR_CL, ncl = gridDim.x / TR_CL;
+  const int64_t base_cta = cid * TR_CL;  // first CTA of this cluster
+  auto scr_of = [&](int r) { return B.scratch + (base_cta + r) * TR_SCRATCH; };
+  auto sync = [&]() {
     __threadfence();
     cluster.sync();
+    return true;
+  };
+  for (int64_t o = cid; o < count; o += ncl) {
+    trunc_part<T, C>(ops[o], terms, B, rk, scr_of, sync, reinterpret_cast<T*>(smraw), ts);
+    sync();
   }
 }
+
+// ---------------------------------------------------------------------------
+// The whole H-Cholesky as one dependency-driven cooperative launch.  The ops
+// of the plan (POTRF, TRSM, GEMM, truncations) are numbered in wave order;
+// each CTA takes the next number from a ticket counter, waits until every
+// producer of that op has signalled, runs it and signals its consumers.  A
+// group truncation is TR_CL consecutive numbers, one per part: its CTAs meet
+// at the start (each publishes its scratch slice) and at every phase of the
+// op through bounded barriers in global memory, and part 0 signals the
+// consumers when all parts are done.  Progress: tickets go out in wave order
+// and producers always have smaller numbers, so the unfinished op with the
+// smallest number either runs (a single-CTA op: its producers are done) or
+// is a group whose remaining parts are the very next tickets, which the next
+// CTAs to finish take (the grid has more than TR_CL CTAs).  Every wait is
+// bounded (kBarrierNs): a CTA that gives up records DEV_TIMEOUT and raises
+// the abort flag, and every CTA leaves.  Each op computes what it computes in
+// the wave launches, after the same producers: the results are the waves'.
+// ---------------------------------------------------------------------------
+template <class T, class C>
+__global__ void __launch_bounds__(TR_THREADS, 1)
+    k_factor(const FlowOp* flow, int64_t nops, const int32_t* npred, const int64_t* succ_off, const int32_t* succ,
+             int32_t* count, const OpPotrf* potrf, const OpTrsm* trsm, const OpGemm* gemm, const OpTrunc* trunc,
+             const TermD* terms, TrGroup* groups, Bases B, GridBar* gb) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ TrShared<C> ts;
+  __shared__ GemmSmem<T> gs;
+  __shared__ long long s_op;
+  __shared__ int s_ok;
+  double* my_scr = B.scratch + (int64_t)blockIdx.x * TR_SCRATCH;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      volatile unsigned int* abort = &gb->abort;
+      long long i = -1;
+      if (!*abort) i = (long long)atomicAdd(&gb->ticket, 1ull);
+      int ok = i >= 0 && i < nops;
+      if (ok) {
+        const volatile int32_t* cnt = count + i;
+        const int32_t need = npred[i];
+        const unsigned long long t0 = global_ns();
+        while (*cnt < need) {
+          if (*abort || global_ns() - t0 > kBarrierNs) {
+            atomicExch(&gb->abort, 1u);
+            record_error(B.status, DEV_TIMEOUT, 2);
+            ok = 0;
+            break;
+          }
+          __nanosleep(20);
+        }
+        __threadfence();
+      }
+      s_op = i;
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    const FlowOp f = flow[s_op];
+    bool done = true;
+    switch (f.type) {
+      case OP_POTRF:
+        do_potrf(potrf[f.idx], B, reinterpret_cast<double*>(smraw));
+        break;
+      case OP_TRSM:
+        do_trsm<T>(trsm[f.idx], B, reinterpret_cast<T*>(smraw));
+        break;
+      case OP_GEMM:
+        do_gemm<T>(gemm[f.idx], B, gs);
+        break;
+      case OP_TRUNC:
+        trunc_one<T, C>(trunc[f.idx], terms, B, my_scr, reinterpret_cast<T*>(smraw), ts);
+        break;
+      default: {  // OP_TRUNC_BIG: part f.part of a group
+        TrGroup* g = groups + f.group;
+        if (threadIdx.x == 0) g->cta[f.part] = (int32_t)blockIdx.x;
+        auto sync = [&]() { return bounded_barrier(&g->count, &g->gen, TR_CL, &gb->abort, B.status); };
+        if (!sync()) return;  // every part has published its scratch slice
+        auto scr_of = [&](int r) {
+          return B.scratch + (int64_t)reinterpret_cast<volatile int32_t*>(g->cta)[r] * TR_SCRATCH;
+        };
+        trunc_part<T, C>(trunc[f.idx], terms, B, f.part, scr_of, sync, reinterpret_cast<T*>(smraw), ts);
+        done = sync();  // all parts finished, the rank is written
+        if (!done) return;
+        if (f.part != 0) continue;  // part 0 signals for the group
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();  // the op's writes before its signals
+      for (int64_t e = succ_off[s_op]; e < succ_off[s_op + 1]; ++e) atomicAdd(count + succ[e], 1);
+    }
+  }
+}
+
+// dynamic shared memory of the factorisation kernel: the truncation chunk
+// or TRSM / POTRF block, whichever is larger
+template <class T, class C>
+static size_t factor_smem(int max_dense);
 
 // dynamic shared memory: the streamed chunk, or the per-warp R factors and
 // update arrays of the warp-level QR, whichever is larger
@@ -979,6 +1100,52 @@ static void launch_pair(const OpTrunc* ops, int64_t count, const TermD* terms, c
     const int64_t ncl = count < cap / TR_CL ? count : cap / TR_CL;
     k_trunc_cl<T, C><<<(int)(ncl * TR_CL), TR_THREADS, sm, st>>>(ops, count, terms, B);
   }
+}
+
+template <class T, class C>
+static size_t factor_smem(int max_dense) {
+  const size_t tr = smem_bytes<T, C>(), blk = trsm_smem(max_dense);
+  return tr > blk ? tr : blk;
+}
+
+template <class T, class C>
+static int launch_factor_t(const Plan& P, const Bases& B, GridBar* gb, int max_dense, cudaStream_t st) {
+  const size_t sm = factor_smem<T, C>(max_dense);
+  if (cudaFuncSetAttribute(k_factor<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+    return -1;
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_factor<T, C>, TR_THREADS, sm) != cudaSuccess) return -1;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int grid = per * sms;
+  if (grid > max_trunc_ctas()) grid = max_trunc_ctas();  // one truncation scratch slice per CTA
+  const int64_t nops = (int64_t)P.flow.size();
+  if (grid <= TR_CL || nops <= 0 || !gb || !P.d_count) return -1;
+  if (cudaMemsetAsync(gb, 0, sizeof(GridBar), st) != cudaSuccess) return -1;
+  if (cudaMemsetAsync(P.d_count, 0, nops * sizeof(int32_t), st) != cudaSuccess) return -1;
+  if (P.ngroups && cudaMemsetAsync(P.d_groups, 0, P.ngroups * sizeof(TrGroup), st) != cudaSuccess) return -1;
+  const FlowOp* flow = P.d_flow;
+  const int32_t* npred = P.d_npred;
+  const int64_t* so = P.d_succ_off;
+  const int32_t* sc = P.d_succ;
+  int32_t* cnt = P.d_count;
+  const OpPotrf* po = P.d_potrf;
+  const OpTrsm* tr = P.d_trsm;
+  const OpGemm* ge = P.d_gemm;
+  const OpTrunc* tu = P.d_trunc;
+  const TermD* te = P.d_terms;
+  TrGroup* gr = P.d_groups;
+  Bases b = B;
+  void* args[] = {(void*)&flow, (void*)&nops, (void*)&npred, (void*)&so, (void*)&sc, (void*)&cnt, (void*)&po,
+                  (void*)&tr, (void*)&ge, (void*)&tu, (void*)&te, (void*)&gr, (void*)&b, (void*)&gb};
+  return cudaLaunchCooperativeKernel((void*)k_factor<T, C>, grid, TR_THREADS, args, sm, st) == cudaSuccess ? 0 : -1;
+}
+
+int launch_factor(const Plan& P, const Bases& B, GridBar* gb, int max_dense, cudaStream_t st) {
+  if (!B.mixed) return launch_factor_t<double, double>(P, B, gb, max_dense, st);
+  if (B.core64) return launch_factor_t<float, double>(P, B, gb, max_dense, st);
+  return launch_factor_t<float, float>(P, B, gb, max_dense, st);
 }
 
 // FP64: FP64 throughout; mixed: FP32 panels with an FP32 core, or with an

@@ -408,6 +408,47 @@ def test_accumulated_updates_vs_oracle(hlc):
         assert abs(r[k] - ho[k]) / 6000 <= 1e-7, (k, r[k], ho[k])
 
 
+_FACTOR_CASE = """
+import json, sys
+sys.path.insert(0, {root!r})
+from paper_1709_08625_gb300 import hlc, inputs
+c = hlc.Context(0)
+out = {{}}
+for prec in (hlc.HLC_FP64, hlc.HLC_MIXED, hlc.HLC_MIXED_SVD64):
+    t = c.build_tree(inputs.points(14000, 1530), leaf=64, eps=1e-6, kmax=128, precision=prec)
+    r = t.loglik(hlc.theta(1.0, 0.05, 0.5, 1e-4), inputs.normal(14000, 1531))
+    out[str(prec)] = {{k: r[k] for k in ("loglik", "logdet", "quad", "quad_factor", "refine_iters", "max_rank_L",
+                                        "bytes_L")}}
+    out[str(prec)]["persistent"] = c.counters(reset=True)["persistent"]
+    t.free()
+print(json.dumps(out))
+"""
+
+
+def test_dataflow_factor_matches_waves(hlc):
+    # the H-Cholesky as one dependency-driven launch (group truncations for
+    # the blocks of more than 4096 rows among them) gives the bits of the
+    # graph-replayed waves, in every precision mode
+    import json
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    runs = {}
+    for flag in ("1", "0"):
+        env = dict(os.environ, HLC_FACTOR_FLOW=flag)
+        out = subprocess.run([sys.executable, "-c", _FACTOR_CASE.format(root=root)], env=env, capture_output=True,
+                             text=True, timeout=900)
+        assert out.returncode == 0, out.stderr[-2000:]
+        runs[flag] = json.loads(out.stdout.strip().splitlines()[-1])
+    for prec in runs["1"]:
+        a, b = dict(runs["1"][prec]), dict(runs["0"][prec])
+        # one more persistent launch per evaluation with the dataflow factor
+        assert a.pop("persistent") == b.pop("persistent") + 1
+        assert a == b, prec
+
+
 # --------------------------------------------------------------------------
 # failure detection: a bounded device wait that runs out
 # --------------------------------------------------------------------------
