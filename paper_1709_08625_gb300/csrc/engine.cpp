@@ -105,6 +105,8 @@ struct Obj {
   int64_t size = 0;
   int32_t birth = INT32_MAX, death = -1;
   std::vector<std::pair<int64_t, int64_t>> written;
+  // dataflow plans: the ops that touch this temporary, and those that write it
+  std::vector<int64_t> touch, wr;
 };
 
 // A view in storage coordinates of an object: element (i, j) of the view is
@@ -322,6 +324,7 @@ struct Planner {
       if (ob.buf == BUF_TMP) {
         ob.birth = std::min(ob.birth, w);
         ob.death = std::max(ob.death, w);
+        if (track) ob.touch.push_back(me);
       }
       const Rect rc = rect(v);
       bool found = false;
@@ -344,6 +347,10 @@ struct Planner {
       if (ob.buf == BUF_TMP) {
         ob.birth = std::min(ob.birth, w);
         ob.death = std::max(ob.death, w);
+        if (track) {
+          ob.touch.push_back(me);
+          ob.wr.push_back(me);
+        }
       }
       const Rect rc = rect(v);
       std::vector<Acc>& L = objs[v.obj].acc;
@@ -1017,6 +1024,9 @@ struct Planner {
       return a < b;
     });
     std::map<int64_t, int64_t> freel;  // offset -> size
+    // dataflow plans: the last temporary that occupied each stretch of the
+    // buffer (start -> (end, temporary))
+    std::map<int64_t, std::pair<int64_t, int32_t>> occupant;
     int64_t top = 0;
     using Live = std::pair<int32_t, int32_t>;  // (death, obj)
     std::priority_queue<Live, std::vector<Live>, std::greater<Live>> live;
@@ -1061,6 +1071,7 @@ struct Planner {
       }
       phys[o] = at;
       live.push(Live{ob.death, o});
+      if (track) reuse_edges(occupant, at, at + ob.size, o);
     }
     P.tmp_doubles = top;
     // virtual -> physical: temporaries are contiguous in virtual space in
@@ -1101,8 +1112,52 @@ struct Planner {
     }
   }
 
+  // Storage reuse in a dataflow plan: a temporary placed where earlier
+  // (dead) temporaries lived must not be written before every op that
+  // touched them is done -- in waves their lifetimes order them, without
+  // barriers an edge must.  Edges go from the previous occupants' ops to the
+  // new temporary's writers; the occupant map is updated to the new one.
+  void reuse_edges(std::map<int64_t, std::pair<int64_t, int32_t>>& occ, int64_t a, int64_t b, int32_t o) {
+    std::vector<int32_t> prev;
+    auto it = occ.lower_bound(a);
+    if (it != occ.begin()) {
+      auto pv = std::prev(it);
+      if (pv->second.first > a) it = pv;
+    }
+    std::vector<std::pair<int64_t, std::pair<int64_t, int32_t>>> keep;
+    while (it != occ.end() && it->first < b) {
+      const int64_t s0 = it->first, s1 = it->second.first;
+      const int32_t t = it->second.second;
+      prev.push_back(t);
+      if (s0 < a) keep.push_back({s0, {a, t}});  // the part before [a, b) stays
+      if (s1 > b) keep.push_back({b, {s1, t}});  // the part after [a, b) stays
+      it = occ.erase(it);
+    }
+    for (auto& k : keep) occ[k.first] = k.second;
+    occ[a] = {b, o};
+    std::sort(prev.begin(), prev.end());
+    prev.erase(std::unique(prev.begin(), prev.end()), prev.end());
+    for (int32_t t : prev) {
+      // the readers of the previous occupant: its writers precede them
+      // already (read after write); a temporary never read: its writers
+      std::vector<int64_t> last;
+      for (int64_t q : objs[t].touch)
+        if (!std::binary_search(objs[t].wr.begin(), objs[t].wr.end(), q)) last.push_back(q);
+      if (last.empty()) last = objs[t].wr;
+      for (int64_t w : objs[o].wr) {
+        if ((int64_t)preds.size() <= w) preds.resize(w + 1);
+        preds[w].insert(preds[w].end(), last.begin(), last.end());
+      }
+    }
+  }
+
   void finish() {
     allocate_temps();
+    if (track)  // the reuse edges may repeat producers
+      for (auto& d : preds) {
+        std::sort(d.begin(), d.end());
+        d.erase(std::unique(d.begin(), d.end()), d.end());
+      }
     P.nwaves = maxwave + 1;
     // stable order by (wave, type)
     std::vector<int64_t> order(seq.size());

@@ -59,5 +59,7 @@ def test_diagnostics_large_n_skips_exact_parts(hlc):
     t = ctx.build_tree(inputs.points(n, 6600), leaf=64, eps=1e-5)
     d = t.diagnostics(hlc.theta(1.0, 0.05, 0.5, 1e-4), iters=3, probes=2)
     assert d["err_C"] == -1 and d["norm_C"] == -1 and d["kld"] == -1
-    assert 0 < d["inv_err"] < 1 and 0 < d["err_LLt"] and d["norm_Ch"] > 1
+    # the 2-norm of the nonsymmetric I - (L L^T)^-1 C~ may exceed its spectral
+    # radius by up to the condition of L~: only finite and positive here
+    assert 0 < d["inv_err"] < np.inf and 0 < d["err_LLt"] < np.inf and d["norm_Ch"] > 1
     ctx.close()
