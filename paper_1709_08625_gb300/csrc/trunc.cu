@@ -987,7 +987,7 @@ __global__ void __cluster_dims__(TR_CL, 1, 1) __launch_bounds__(TR_THREADS, size
 // the wave launches, after the same producers: the results are the waves'.
 // ---------------------------------------------------------------------------
 template <class T, class C>
-__global__ void __launch_bounds__(TR_THREADS, 1)
+__global__ void __launch_bounds__(TR_THREADS, sizeof(T) == 4 ? 2 : 1)
     k_factor(const FlowOp* flow, int64_t nops, const int32_t* npred, const int64_t* succ_off, const int32_t* succ,
              int32_t* count, const OpPotrf* potrf, const OpTrsm* trsm, const OpGemm* gemm, const OpTrunc* trunc,
              const TermD* terms, TrGroup* groups, Bases B, GridBar* gb) {
