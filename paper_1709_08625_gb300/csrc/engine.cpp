@@ -693,8 +693,11 @@ struct Planner {
       gemm(Tv, T_(U(a)), X, rk(a), dim(A.m, NOSLOT), c, 1.0);
       gemm(Y, V(a), Tv, dim(A.n, NOSLOT), rk(a), c, alpha);
     } else {
+      // children from the bottom row of blocks up: in the backward solve the
+      // bottom rows of X are final first, and the products accumulate into
+      // Y in this order, so no contribution waits behind a later one
       const int64_t r0 = rlo(a), s0 = slo(a);
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 3; q >= 0; --q) {
         const int32_t cb = A.ch[q];
         if (cb < 0) continue;
         const Cluster& cr = T.cl[blk(cb).r];

@@ -350,41 +350,52 @@ __global__ void __launch_bounds__(256) k_flow(const FlowOp* flow, int64_t nops, 
   __shared__ GemmSmem<double> gd;
   __shared__ GemmSmem<float> gf;
   __shared__ long long s_op;
-  __shared__ int s_ok;
+  __shared__ int s_ok, s_go;
   unsigned long long* ticket = &gb->ticket;
   for (;;) {
     if (threadIdx.x == 0) {
       volatile unsigned int* abort = &gb->abort;
       long long i = -1;
       if (!*abort) i = (long long)atomicAdd(ticket, 1ull);
-      int ok = i >= 0 && i < nops;
-      if (ok) {
-        // wait for the producers of op i
-        const volatile int32_t* cnt = count + i;
-        const int32_t need = npred[i];
-        const unsigned long long t0 = global_ns();
-        while (*cnt < need) {
-          if (*abort || global_ns() - t0 > kBarrierNs) {
-            atomicExch(&gb->abort, 1u);
-            record_error(B.status, DEV_TIMEOUT, 1);
-            ok = 0;
-            break;
-          }
-          __nanosleep(20);
-        }
-        __threadfence();
-      }
       s_op = i;
-      s_ok = ok;
+      s_ok = i >= 0 && i < nops;
     }
     __syncthreads();
     if (!s_ok) return;
     const FlowOp f = flow[s_op];
+    // a solve's factor block is final: load it while the producers finish
     if (f.type == OP_TRSM) {
       if (B.mixed)
-        do_trsm<float>(trsm[f.idx], B, reinterpret_cast<float*>(sL));
+        trsm_load<float>(trsm[f.idx], B, reinterpret_cast<float*>(sL));
       else
-        do_trsm<double>(trsm[f.idx], B, sL);
+        trsm_load<double>(trsm[f.idx], B, sL);
+    }
+    if (threadIdx.x == 0) {
+      // wait for the producers of the op
+      volatile unsigned int* abort = &gb->abort;
+      const volatile int32_t* cnt = count + s_op;
+      const int32_t need = npred[s_op];
+      const unsigned long long t0 = global_ns();
+      int ok = 1;
+      while (*cnt < need) {
+        if (*abort || global_ns() - t0 > kBarrierNs) {
+          atomicExch(&gb->abort, 1u);
+          record_error(B.status, DEV_TIMEOUT, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(20);
+      }
+      __threadfence();
+      s_go = ok;  // not s_ok: another thread may still be reading it
+    }
+    __syncthreads();
+    if (!s_go) return;
+    if (f.type == OP_TRSM) {
+      if (B.mixed)
+        trsm_apply<float>(trsm[f.idx], B, reinterpret_cast<const float*>(sL));
+      else
+        trsm_apply<double>(trsm[f.idx], B, sL);
     } else if (B.mixed) {
       do_gemm<float>(gemm[f.idx], B, gf);
     } else {

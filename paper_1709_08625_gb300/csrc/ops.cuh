@@ -84,12 +84,11 @@ inline __device__ void do_potrf(const OpPotrf& op, const Bases& B, double* sm) {
 // sequential substitution chain multiplies instead of dividing.
 // sL: n * n + n entries of T.
 // ---------------------------------------------------------------------------
+// The block L and the reciprocals of its diagonal into shared memory (does
+// not touch X: in a solve, where L is final, it may run before X is).
 template <class T>
-__device__ void do_trsm(const OpTrsm& op, const Bases& B, T* sL) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+__device__ void trsm_load(const OpTrsm& op, const Bases& B, T* sL) {
   const int n = op.n;
-  const int c = dimv(op.c, B.ranks);
-  if (B.flops && threadIdx.x == 0) atomicAdd(B.flops + OP_TRSM, (double)n * n * c);
   const double* L = vptr(B, op.L);
   T* sInv = sL + n * n;
   // the block through registers, LD_BATCH loads in flight per thread
@@ -108,6 +107,16 @@ __device__ void do_trsm(const OpTrsm& op, const Bases& B, T* sL) {
   }
   for (int i = threadIdx.x; i < n; i += blockDim.x) sInv[i] = T(1) / (T)L[i * op.L.rs + i * op.L.cs];
   __syncthreads();
+}
+
+// The substitution (or product) against X with L already in shared memory.
+template <class T>
+__device__ void trsm_apply(const OpTrsm& op, const Bases& B, const T* sL) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int n = op.n;
+  const int c = dimv(op.c, B.ranks);
+  if (B.flops && threadIdx.x == 0) atomicAdd(B.flops + OP_TRSM, (double)n * n * c);
+  const T* sInv = sL + n * n;
   double* X = vptr(B, op.X);
   for (int col = w; col < c; col += nw) {
     double* xc = X + col * op.X.cs;
@@ -171,6 +180,12 @@ __device__ void do_trsm(const OpTrsm& op, const Bases& B, T* sL) {
     }
   }
   __syncthreads();
+}
+
+template <class T>
+__device__ void do_trsm(const OpTrsm& op, const Bases& B, T* sL) {
+  trsm_load<T>(op, B, sL);
+  trsm_apply<T>(op, B, sL);
 }
 
 

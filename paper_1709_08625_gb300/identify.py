@@ -24,10 +24,13 @@ from . import hlc, inputs
 
 
 def run(n0=524288, n=65536, seed=0, true=(1.0, 0.0864, 0.5), nugget=1e-4, start=None, eps=1e-6, leaf=64,
-        precision="mixed", max_iter=200, size_tol=1e-5, device=0, trace=False):
+        precision="mixed", max_iter=200, size_tol=1e-5, device=0, trace=False, gen_precision=None):
     """Returns a dict: the true and identified theta, the fit's record and
-    the wall times of the generation and the fit."""
-    prec = {"fp64": hlc.HLC_FP64, "mixed": hlc.HLC_MIXED, "mixed_svd64": hlc.HLC_MIXED_SVD64}[precision]
+    the wall times of the generation and the fit.  gen_precision: precision
+    of the factor that draws Z0 (default: the fit's)."""
+    modes = {"fp64": hlc.HLC_FP64, "mixed": hlc.HLC_MIXED, "mixed_svd64": hlc.HLC_MIXED_SVD64}
+    prec = modes[precision]
+    gprec = modes[gen_precision or precision]
     s2, ell, nu = true
     if start is None:
         start = (1.2 * s2, 1.25 * ell, 0.8 * nu)
@@ -37,7 +40,7 @@ def run(n0=524288, n=65536, seed=0, true=(1.0, 0.0864, 0.5), nugget=1e-4, start=
     ctx = hlc.Context(device)
     try:
         t0 = time.perf_counter()
-        tree0 = ctx.build_tree(xy0, leaf=leaf, eps=eps, precision=hlc.HLC_FP64)
+        tree0 = ctx.build_tree(xy0, leaf=leaf, eps=eps, precision=gprec)
         z0 = tree0.sample(hlc.theta(s2, ell, nu, nugget), xi)
         tree0.free()
         t_gen = time.perf_counter() - t0
@@ -50,7 +53,8 @@ def run(n0=524288, n=65536, seed=0, true=(1.0, 0.0864, 0.5), nugget=1e-4, start=
         r, tr = tree.fit(z, st, trace_cap=4 * max_iter + 16 if trace else 0, max_iter=max_iter,
                          size_tol=size_tol)
         t_fit = time.perf_counter() - t0
-        out = dict(n0=n0, n=n, seed=seed, eps=eps, leaf=leaf, precision=precision, nugget=nugget,
+        out = dict(n0=n0, n=n, seed=seed, eps=eps, leaf=leaf, precision=precision,
+                   gen_precision=gen_precision or precision, nugget=nugget,
                    true=dict(sigma2=s2, ell=ell, nu=nu), start=dict(sigma2=start[0], ell=start[1], nu=start[2]),
                    estimate=dict(sigma2=r["sigma2"], ell=r["ell"], nu=r["nu"]), loglik_start=l_start, fit=r,
                    seconds_generate=t_gen, seconds_fit=t_fit,
