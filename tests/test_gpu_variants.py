@@ -41,13 +41,14 @@ def test_variant_trees_match_oracle(ctx, n, leaf, eta, adm, split):
 
 @pytest.mark.parametrize("n,adm,split,nu,ell,eps,nugget", [(4000, 1, 0, 0.5, 0.05, 1e-7, 1e-4),
                                                            (4000, 0, 1, 1.5, 0.05, 1e-7, 1e-4),
-                                                           (2000, 2, 0, 0.5, 0.1, 1e-7, 1e-2),
+                                                           (2000, 2, 0, 0.5, 0.1, 1e-6, 1e-2),
                                                            (4000, 2, 1, 1.0, 0.1, 1e-5, 1e-4)])
 def test_variant_loglik_vs_oracle(ctx, hlc, n, adm, split, nu, ell, eps, nugget):
     # weak admissibility makes neighbouring clusters low-rank: their ranks
     # grow fast as eps falls, and at eps = 1e-5 the approximation of the
     # neighbours can leave C~ indefinite (the failure of Sec. 3); its
-    # geometric-split case runs on fewer points at eps = 1e-7
+    # geometric-split case runs on fewer points at eps = 1e-6, where partial
+    # pivoting still stops within 128 columns (111 in the oracle)
     xy = inputs.points(n, 8100)
     z = inputs.normal(n, 8101)
     th = (1.0, ell, nu, nugget)
@@ -56,6 +57,27 @@ def test_variant_loglik_vs_oracle(ctx, hlc, n, adm, split, nu, ell, eps, nugget)
     ho = oracle.h_loglik(xy, z, *th, eps, leaf=64, admissibility=adm, split=split)
     assert abs(r["loglik"] - ho["loglik"]) / n <= 1e-7
     assert abs(r["logdet"] - ho["logdet"]) / n <= 1e-7
+
+
+def test_weak_admissibility_rank_capacity(ctx, hlc):
+    # the same weak-admissibility case at eps = 1e-7: ACA with partial
+    # pivoting needs 142 columns on the largest neighbour block (oracle,
+    # before recompression), above the 128 the device kernel holds, so the
+    # evaluation reports HLC_ERR_RANK and the context stays usable
+    n = 2000
+    xy = inputs.points(n, 8100)
+    z = inputs.normal(n, 8101)
+    H = oracle.HOracle(xy, leaf=64, admissibility=2)
+    H.set_theta(1.0, 0.1, 0.5, 1e-2)
+    need = max(H.aca_block(r0, r1 - r0, c0, c1 - c0, 1e-7, recompress=False)[0].shape[1]
+               for r0, r1, c0, c1, a in H.leaf_blocks() if a == 1)
+    assert need > 128
+    t = ctx.build_tree(xy, leaf=64, eps=1e-7, kmax=128, admissibility=2)
+    with pytest.raises(hlc.HlcError) as e:
+        t.loglik(hlc.theta(1.0, 0.1, 0.5, 1e-2), z)
+    assert e.value.status == hlc.HLC_ERR_RANK
+    t2 = ctx.build_tree(xy, leaf=64, eps=1e-6, kmax=128, admissibility=2)
+    assert np.isfinite(t2.loglik(hlc.theta(1.0, 0.1, 0.5, 1e-2), z)["loglik"])
 
 
 @pytest.mark.parametrize("k", [10, 16, 24])
