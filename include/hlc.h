@@ -54,6 +54,11 @@
  *                     at exit
  *   HLC_PHASES=1      count clock cycles per phase of the truncation kernel and
  *                     print them when the context is destroyed
+ *   HLC_FACTOR_TRACE=<path>  record the dependency-driven factorisation's
+ *                     timeline (per op: taken, ready, done, CTA, releasing
+ *                     producer) and write it to <path> after every
+ *                     factorisation (paper_1709_08625_gb300/factor_trace.py
+ *                     reads it)
  */
 #ifndef HLC_H
 #define HLC_H

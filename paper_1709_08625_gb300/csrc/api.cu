@@ -694,6 +694,69 @@ int do_assemble(hlc_tree* t, const hlc_theta* th, hlc_hmat* C) {
   return st;
 }
 
+// HLC_FACTOR_TRACE=<path>: the dataflow factorisation records a timeline
+// (FactorTrace per op) and writes it to <path> after the launch.  File: the
+// 8 bytes "HLCFTR01", int64 nops, then nops records of six int32 (type, part
+// and four sizes: POTRF n; TRSM n, c, trans; GEMM m, k, c; truncations m, n,
+// term columns, rank after), then the nops FactorTrace records.  Sizes that
+// are ranks are read after the factorisation (a temporary's slot holds its
+// last value).
+const char* factor_trace_path() {
+  static const char* p = getenv("HLC_FACTOR_TRACE");
+  return p && p[0] ? p : nullptr;
+}
+
+int write_factor_trace(hlc_tree* t, const hlc_hmat* L, const FactorTrace* d_trace, const char* path) {
+  hlc_ctx* c = t->ctx;
+  const Plan& P = t->chol;
+  const int64_t nops = (int64_t)P.flow.size();
+  std::vector<FactorTrace> tr(nops);
+  const int64_t nsl = (int64_t)t->T.nslots + P.tmp_slots;
+  std::vector<int> rk(std::max<int64_t>(nsl, 1));
+  CK(cudaMemcpyAsync(tr.data(), d_trace, nops * sizeof(FactorTrace), cudaMemcpyDeviceToHost, c->stream));
+  if (nsl) CK(cudaMemcpyAsync(rk.data(), L->ranks, nsl * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  auto dim = [&](const Dim& d) { return d.slot >= 0 && d.slot < nsl ? rk[d.slot] : d.n; };
+  std::vector<int32_t> meta(6 * nops, 0);
+  for (int64_t i = 0; i < nops; ++i) {
+    const FlowOp& f = P.flow[i];
+    int32_t* m = &meta[6 * i];
+    m[0] = f.type;
+    m[1] = f.part;
+    if (f.type == OP_POTRF) {
+      m[2] = P.potrf[f.idx].n;
+    } else if (f.type == OP_TRSM) {
+      const OpTrsm& o = P.trsm[f.idx];
+      m[2] = o.n;
+      m[3] = dim(o.c);
+      m[4] = o.trans;
+    } else if (f.type == OP_GEMM) {
+      const OpGemm& o = P.gemm[f.idx];
+      m[2] = dim(o.m);
+      m[3] = dim(o.k);
+      m[4] = dim(o.c);
+    } else {
+      const OpTrunc& o = P.trunc[f.idx];
+      m[2] = o.m;
+      m[3] = o.n;
+      int64_t cols = 0;
+      for (int64_t e = o.term0; e < o.term0 + o.nterms; ++e) {
+        const TermD& d = P.terms[e];
+        cols += (d.flags & 1) ? d.urows : (d.flags & 2) ? d.vrows : dim(d.k);
+      }
+      m[4] = (int32_t)cols;
+      m[5] = o.slot >= 0 && o.slot < nsl ? rk[o.slot] : -1;
+    }
+  }
+  FILE* fp = fopen(path, "wb");
+  if (!fp) return HLC_ERR_ARG;
+  bool ok = fwrite("HLCFTR01", 1, 8, fp) == 8 && fwrite(&nops, sizeof(nops), 1, fp) == 1 &&
+            fwrite(meta.data(), sizeof(int32_t), meta.size(), fp) == meta.size() &&
+            fwrite(tr.data(), sizeof(FactorTrace), tr.size(), fp) == tr.size();
+  ok = (fclose(fp) == 0) && ok;
+  return ok ? HLC_OK : HLC_ERR_ARG;
+}
+
 int do_cholesky(hlc_tree* t, const hlc_hmat* C, hlc_hmat* L) {
   hlc_ctx* c = t->ctx;
   int st = build_plans(t, true, false);
@@ -708,13 +771,24 @@ int do_cholesky(hlc_tree* t, const hlc_hmat* C, hlc_hmat* L) {
   bool flowed = false;
   if (factor_flow_enabled() && c->persistent && !c->profiling && !g_prof.on && t->chol.d_flow) {
     const int md = (int)std::max<int64_t>(t->T.max_dense_dim, t->T.leaf);
-    if (launch_factor(t->chol, B, c->d_gridbar, md, c->stream) == 0) {
+    const char* tpath = factor_trace_path();
+    FactorTrace* d_trace = nullptr;
+    if (tpath) {
+      const size_t bytes = t->chol.flow.size() * sizeof(FactorTrace);
+      CK(cudaMalloc(&d_trace, bytes));
+      // releaser -1 where no producer signals
+      CK(cudaMemsetAsync(d_trace, 0xff, bytes, c->stream));
+    }
+    if (launch_factor(t->chol, B, c->d_gridbar, md, d_trace, c->stream) == 0) {
       flowed = true;
       c->launches += 1;
       c->persistent_launches += 1;
+      if (d_trace) st = write_factor_trace(t, L, d_trace, tpath);
     } else {
       cudaGetLastError();
     }
+    if (d_trace) CK(cudaFree(d_trace));
+    if (st) return st;
   }
   if (!flowed) run_plan(t, t->chol, B, c->stream);
   CK(cudaGetLastError());

@@ -221,6 +221,16 @@ struct TrGroup {
   int32_t cta[8];
 };
 
+// Timeline record of one op of the dataflow factorisation (optional): global
+// timer nanoseconds when a CTA took the op's ticket, when its producers were
+// done and when it finished; the CTA; the producer whose signal released it
+// (-1: none, the op had no producers).
+struct FactorTrace {
+  unsigned long long t_take, t_ready, t_done;
+  uint32_t cta;
+  int32_t releaser;
+};
+
 struct Plan {
   std::vector<OpGemm> gemm;
   std::vector<OpTrsm> trsm;

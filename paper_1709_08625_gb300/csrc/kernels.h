@@ -33,7 +33,8 @@ int waves_max_per_sm(int max_dense);
 // when the cooperative launch is unavailable.
 // The whole factorisation plan (its dataflow form) as one dependency-driven
 // cooperative launch; -1 when the launch is unavailable.
-int launch_factor(const Plan& P, const Bases& B, GridBar* gb, int max_dense, cudaStream_t st);
+int launch_factor(const Plan& P, const Bases& B, GridBar* gb, int max_dense, FactorTrace* trace,
+                  cudaStream_t st);
 int launch_flow(const FlowOp* flow, int64_t nops, const int32_t* npred, const int64_t* succ_off, const int32_t* succ,
                 int32_t* count, const OpTrsm* trsm, const OpGemm* gemm, const Bases& B, GridBar* gb, int max_dense,
                 int per_sm, cudaStream_t st);

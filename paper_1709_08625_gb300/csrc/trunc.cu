@@ -985,12 +985,15 @@ __global__ void __cluster_dims__(TR_CL, 1, 1) __launch_bounds__(TR_THREADS, size
 // bounded (kBarrierNs): a CTA that gives up records DEV_TIMEOUT and raises
 // the abort flag, and every CTA leaves.  Each op computes what it computes in
 // the wave launches, after the same producers: the results are the waves'.
+// With a trace buffer (FactorTrace per op) the kernel records when each op
+// was taken, became ready and finished, its CTA, and the producer whose
+// signal released it.
 // ---------------------------------------------------------------------------
 template <class T, class C>
 __global__ void __launch_bounds__(TR_THREADS, sizeof(T) == 4 ? 2 : 1)
     k_factor(const FlowOp* flow, int64_t nops, const int32_t* npred, const int64_t* succ_off, const int32_t* succ,
              int32_t* count, const OpPotrf* potrf, const OpTrsm* trsm, const OpGemm* gemm, const OpTrunc* trunc,
-             const TermD* terms, TrGroup* groups, Bases B, GridBar* gb) {
+             const TermD* terms, TrGroup* groups, Bases B, GridBar* gb, FactorTrace* trace) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ TrShared<C> ts;
   __shared__ GemmSmem<T> gs;
@@ -1003,6 +1006,10 @@ __global__ void __launch_bounds__(TR_THREADS, sizeof(T) == 4 ? 2 : 1)
       long long i = -1;
       if (!*abort) i = (long long)atomicAdd(&gb->ticket, 1ull);
       int ok = i >= 0 && i < nops;
+      if (ok && trace) {
+        trace[i].t_take = global_ns();
+        trace[i].cta = (uint32_t)blockIdx.x;
+      }
       if (ok) {
         const volatile int32_t* cnt = count + i;
         const int32_t need = npred[i];
@@ -1017,6 +1024,7 @@ __global__ void __launch_bounds__(TR_THREADS, sizeof(T) == 4 ? 2 : 1)
           __nanosleep(20);
         }
         __threadfence();
+        if (trace) trace[i].t_ready = global_ns();
       }
       s_op = i;
       s_ok = ok;
@@ -1049,13 +1057,24 @@ __global__ void __launch_bounds__(TR_THREADS, sizeof(T) == 4 ? 2 : 1)
         trunc_part<T, C>(trunc[f.idx], terms, B, f.part, scr_of, sync, reinterpret_cast<T*>(smraw), ts);
         done = sync();  // all parts finished, the rank is written
         if (!done) return;
-        if (f.part != 0) continue;  // part 0 signals for the group
+        if (f.part != 0) {  // part 0 signals for the group
+          if (trace && threadIdx.x == 0) trace[s_op].t_done = global_ns();
+          continue;
+        }
       }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();  // the op's writes before its signals
-      for (int64_t e = succ_off[s_op]; e < succ_off[s_op + 1]; ++e) atomicAdd(count + succ[e], 1);
+      if (trace) {
+        trace[s_op].t_done = global_ns();
+        for (int64_t e = succ_off[s_op]; e < succ_off[s_op + 1]; ++e) {
+          const int32_t v = succ[e];
+          if (atomicAdd(count + v, 1) + 1 == npred[v]) trace[v].releaser = (int32_t)s_op;
+        }
+      } else {
+        for (int64_t e = succ_off[s_op]; e < succ_off[s_op + 1]; ++e) atomicAdd(count + succ[e], 1);
+      }
     }
   }
 }
@@ -1109,7 +1128,8 @@ static size_t factor_smem(int max_dense) {
 }
 
 template <class T, class C>
-static int launch_factor_t(const Plan& P, const Bases& B, GridBar* gb, int max_dense, cudaStream_t st) {
+static int launch_factor_t(const Plan& P, const Bases& B, GridBar* gb, int max_dense, FactorTrace* trace,
+                           cudaStream_t st) {
   const size_t sm = factor_smem<T, C>(max_dense);
   if (cudaFuncSetAttribute(k_factor<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
     return -1;
@@ -1138,14 +1158,14 @@ static int launch_factor_t(const Plan& P, const Bases& B, GridBar* gb, int max_d
   TrGroup* gr = P.d_groups;
   Bases b = B;
   void* args[] = {(void*)&flow, (void*)&nops, (void*)&npred, (void*)&so, (void*)&sc, (void*)&cnt, (void*)&po,
-                  (void*)&tr, (void*)&ge, (void*)&tu, (void*)&te, (void*)&gr, (void*)&b, (void*)&gb};
+                  (void*)&tr, (void*)&ge, (void*)&tu, (void*)&te, (void*)&gr, (void*)&b, (void*)&gb, (void*)&trace};
   return cudaLaunchCooperativeKernel((void*)k_factor<T, C>, grid, TR_THREADS, args, sm, st) == cudaSuccess ? 0 : -1;
 }
 
-int launch_factor(const Plan& P, const Bases& B, GridBar* gb, int max_dense, cudaStream_t st) {
-  if (!B.mixed) return launch_factor_t<double, double>(P, B, gb, max_dense, st);
-  if (B.core64) return launch_factor_t<float, double>(P, B, gb, max_dense, st);
-  return launch_factor_t<float, float>(P, B, gb, max_dense, st);
+int launch_factor(const Plan& P, const Bases& B, GridBar* gb, int max_dense, FactorTrace* trace, cudaStream_t st) {
+  if (!B.mixed) return launch_factor_t<double, double>(P, B, gb, max_dense, trace, st);
+  if (B.core64) return launch_factor_t<float, double>(P, B, gb, max_dense, trace, st);
+  return launch_factor_t<float, float>(P, B, gb, max_dense, trace, st);
 }
 
 // FP64: FP64 throughout; mixed: FP32 panels with an FP32 core, or with an
