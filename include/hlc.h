@@ -59,6 +59,9 @@
  *                     producer) and write it to <path> after every
  *                     factorisation (paper_1709_08625_gb300/factor_trace.py
  *                     reads it)
+ *   HLC_SOLVE_TRACE=<path>   the same timeline for every dependency-driven
+ *                     solve or matvec, written to <path>.fwd, <path>.bwd and
+ *                     <path>.mv (the last run of each plan)
  */
 #ifndef HLC_H
 #define HLC_H

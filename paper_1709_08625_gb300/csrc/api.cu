@@ -297,10 +297,79 @@ bool flow_enabled() {
 
 // One persistent launch of a TRSM/GEMM plan: dependency-driven when the plan
 // has its dataflow form, else wave by wave.  0 or -1 (launch unavailable).
-int launch_persistent(const Plan& P, const Bases& B, GridBar* gb, int md, int per, cudaStream_t st) {
+// HLC_FACTOR_TRACE=<path> (HLC_SOLVE_TRACE=<path>): the dataflow
+// factorisation (each dataflow solve or matvec) records a timeline
+// (FactorTrace per op) and writes it to <path> (<path>.<plan>, the plan's
+// last run) after the launch.  File: the 8 bytes "HLCFTR01", int64 nops,
+// then nops records of six int32 (type, part and four sizes: POTRF n; TRSM n,
+// c, trans; GEMM m, k, c; truncations m, n, term columns, rank after), then
+// the nops FactorTrace records.  Sizes that are ranks are read after the run
+// (a temporary's slot holds its last value).
+const char* factor_trace_path() {
+  static const char* p = getenv("HLC_FACTOR_TRACE");
+  return p && p[0] ? p : nullptr;
+}
+
+const char* solve_trace_path() {
+  static const char* p = getenv("HLC_SOLVE_TRACE");
+  return p && p[0] ? p : nullptr;
+}
+
+int write_trace(hlc_tree* t, const Plan& P, const int* d_ranks, int64_t nsl, const FactorTrace* d_trace,
+                const std::string& path) {
+  hlc_ctx* c = t->ctx;
+  const int64_t nops = (int64_t)P.flow.size();
+  std::vector<FactorTrace> tr(nops);
+  std::vector<int> rk(std::max<int64_t>(nsl, 1));
+  CK(cudaMemcpyAsync(tr.data(), d_trace, nops * sizeof(FactorTrace), cudaMemcpyDeviceToHost, c->stream));
+  if (nsl) CK(cudaMemcpyAsync(rk.data(), d_ranks, nsl * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  auto dim = [&](const Dim& d) { return d.slot >= 0 && d.slot < nsl ? rk[d.slot] : d.n; };
+  std::vector<int32_t> meta(6 * nops, 0);
+  for (int64_t i = 0; i < nops; ++i) {
+    const FlowOp& f = P.flow[i];
+    int32_t* m = &meta[6 * i];
+    m[0] = f.type;
+    m[1] = f.part;
+    if (f.type == OP_POTRF) {
+      m[2] = P.potrf[f.idx].n;
+    } else if (f.type == OP_TRSM) {
+      const OpTrsm& o = P.trsm[f.idx];
+      m[2] = o.n;
+      m[3] = dim(o.c);
+      m[4] = o.trans;
+    } else if (f.type == OP_GEMM) {
+      const OpGemm& o = P.gemm[f.idx];
+      m[2] = dim(o.m);
+      m[3] = dim(o.k);
+      m[4] = dim(o.c);
+    } else {
+      const OpTrunc& o = P.trunc[f.idx];
+      m[2] = o.m;
+      m[3] = o.n;
+      int64_t cols = 0;
+      for (int64_t e = o.term0; e < o.term0 + o.nterms; ++e) {
+        const TermD& d = P.terms[e];
+        cols += (d.flags & 1) ? d.urows : (d.flags & 2) ? d.vrows : dim(d.k);
+      }
+      m[4] = (int32_t)cols;
+      m[5] = o.slot >= 0 && o.slot < nsl ? rk[o.slot] : -1;
+    }
+  }
+  FILE* fp = fopen(path.c_str(), "wb");
+  if (!fp) return HLC_ERR_ARG;
+  bool ok = fwrite("HLCFTR01", 1, 8, fp) == 8 && fwrite(&nops, sizeof(nops), 1, fp) == 1 &&
+            fwrite(meta.data(), sizeof(int32_t), meta.size(), fp) == meta.size() &&
+            fwrite(tr.data(), sizeof(FactorTrace), tr.size(), fp) == tr.size();
+  ok = (fclose(fp) == 0) && ok;
+  return ok ? HLC_OK : HLC_ERR_ARG;
+}
+
+int launch_persistent(const Plan& P, const Bases& B, GridBar* gb, int md, int per, cudaStream_t st,
+                      FactorTrace* trace = nullptr) {
   if (flow_enabled() && P.d_flow && P.d_count)
     return launch_flow(P.d_flow, (int64_t)P.flow.size(), P.d_npred, P.d_succ_off, P.d_succ, P.d_count, P.d_trsm,
-                       P.d_gemm, B, gb, md, per, st);
+                       P.d_gemm, B, gb, md, per, trace, st);
   return launch_waves(P.d_waves, (int)P.waves.size(), P.d_trsm, P.d_gemm, P.d_chain, P.chains(), B, gb, md, per, st);
 }
 
@@ -338,7 +407,17 @@ void run_plan(hlc_tree* t, const Plan& P, const Bases& B, cudaStream_t st) {
       }
       if (e0 && e1) cudaEventRecord(e0, st);
     }
-    if (launch_persistent(P, B, c->d_gridbar, md, per, st) == 0) {
+    FactorTrace* d_trace = nullptr;
+    const char* tpath = P.d_flow && flow_enabled() ? solve_trace_path() : nullptr;
+    if (tpath && cudaMalloc(&d_trace, P.flow.size() * sizeof(FactorTrace)) == cudaSuccess)
+      cudaMemsetAsync(d_trace, 0xff, P.flow.size() * sizeof(FactorTrace), st);
+    const int lst = launch_persistent(P, B, c->d_gridbar, md, per, st, d_trace);
+    if (d_trace) {
+      const char* name = &P == &t->fwd ? "fwd" : &P == &t->bwd ? "bwd" : &P == &t->mv ? "mv" : "other";
+      if (lst == 0) write_trace(t, P, B.ranks, t->T.nslots, d_trace, std::string(tpath) + "." + name);
+      cudaFree(d_trace);
+    }
+    if (lst == 0) {
       c->launches += 1;
       c->persistent_launches += 1;
       if (cand >= 0) {
@@ -694,69 +773,6 @@ int do_assemble(hlc_tree* t, const hlc_theta* th, hlc_hmat* C) {
   return st;
 }
 
-// HLC_FACTOR_TRACE=<path>: the dataflow factorisation records a timeline
-// (FactorTrace per op) and writes it to <path> after the launch.  File: the
-// 8 bytes "HLCFTR01", int64 nops, then nops records of six int32 (type, part
-// and four sizes: POTRF n; TRSM n, c, trans; GEMM m, k, c; truncations m, n,
-// term columns, rank after), then the nops FactorTrace records.  Sizes that
-// are ranks are read after the factorisation (a temporary's slot holds its
-// last value).
-const char* factor_trace_path() {
-  static const char* p = getenv("HLC_FACTOR_TRACE");
-  return p && p[0] ? p : nullptr;
-}
-
-int write_factor_trace(hlc_tree* t, const hlc_hmat* L, const FactorTrace* d_trace, const char* path) {
-  hlc_ctx* c = t->ctx;
-  const Plan& P = t->chol;
-  const int64_t nops = (int64_t)P.flow.size();
-  std::vector<FactorTrace> tr(nops);
-  const int64_t nsl = (int64_t)t->T.nslots + P.tmp_slots;
-  std::vector<int> rk(std::max<int64_t>(nsl, 1));
-  CK(cudaMemcpyAsync(tr.data(), d_trace, nops * sizeof(FactorTrace), cudaMemcpyDeviceToHost, c->stream));
-  if (nsl) CK(cudaMemcpyAsync(rk.data(), L->ranks, nsl * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
-  auto dim = [&](const Dim& d) { return d.slot >= 0 && d.slot < nsl ? rk[d.slot] : d.n; };
-  std::vector<int32_t> meta(6 * nops, 0);
-  for (int64_t i = 0; i < nops; ++i) {
-    const FlowOp& f = P.flow[i];
-    int32_t* m = &meta[6 * i];
-    m[0] = f.type;
-    m[1] = f.part;
-    if (f.type == OP_POTRF) {
-      m[2] = P.potrf[f.idx].n;
-    } else if (f.type == OP_TRSM) {
-      const OpTrsm& o = P.trsm[f.idx];
-      m[2] = o.n;
-      m[3] = dim(o.c);
-      m[4] = o.trans;
-    } else if (f.type == OP_GEMM) {
-      const OpGemm& o = P.gemm[f.idx];
-      m[2] = dim(o.m);
-      m[3] = dim(o.k);
-      m[4] = dim(o.c);
-    } else {
-      const OpTrunc& o = P.trunc[f.idx];
-      m[2] = o.m;
-      m[3] = o.n;
-      int64_t cols = 0;
-      for (int64_t e = o.term0; e < o.term0 + o.nterms; ++e) {
-        const TermD& d = P.terms[e];
-        cols += (d.flags & 1) ? d.urows : (d.flags & 2) ? d.vrows : dim(d.k);
-      }
-      m[4] = (int32_t)cols;
-      m[5] = o.slot >= 0 && o.slot < nsl ? rk[o.slot] : -1;
-    }
-  }
-  FILE* fp = fopen(path, "wb");
-  if (!fp) return HLC_ERR_ARG;
-  bool ok = fwrite("HLCFTR01", 1, 8, fp) == 8 && fwrite(&nops, sizeof(nops), 1, fp) == 1 &&
-            fwrite(meta.data(), sizeof(int32_t), meta.size(), fp) == meta.size() &&
-            fwrite(tr.data(), sizeof(FactorTrace), tr.size(), fp) == tr.size();
-  ok = (fclose(fp) == 0) && ok;
-  return ok ? HLC_OK : HLC_ERR_ARG;
-}
-
 int do_cholesky(hlc_tree* t, const hlc_hmat* C, hlc_hmat* L) {
   hlc_ctx* c = t->ctx;
   int st = build_plans(t, true, false);
@@ -783,7 +799,7 @@ int do_cholesky(hlc_tree* t, const hlc_hmat* C, hlc_hmat* L) {
       flowed = true;
       c->launches += 1;
       c->persistent_launches += 1;
-      if (d_trace) st = write_factor_trace(t, L, d_trace, tpath);
+      if (d_trace) st = write_trace(t, t->chol, L->ranks, (int64_t)t->T.nslots + t->chol.tmp_slots, d_trace, tpath);
     } else {
       cudaGetLastError();
     }

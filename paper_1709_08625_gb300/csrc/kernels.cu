@@ -345,7 +345,8 @@ __global__ void __launch_bounds__(256) k_waves(const WaveRange* waves, int nwave
 // relative to the ops it depends on: the results are those of the waves.
 __global__ void __launch_bounds__(256) k_flow(const FlowOp* flow, int64_t nops, const int32_t* npred,
                                               const int64_t* succ_off, const int32_t* succ, int32_t* count,
-                                              const OpTrsm* trsm, const OpGemm* gemm, Bases B, GridBar* gb) {
+                                              const OpTrsm* trsm, const OpGemm* gemm, Bases B, GridBar* gb,
+                                              FactorTrace* trace) {
   extern __shared__ double sL[];
   __shared__ GemmSmem<double> gd;
   __shared__ GemmSmem<float> gf;
@@ -359,6 +360,10 @@ __global__ void __launch_bounds__(256) k_flow(const FlowOp* flow, int64_t nops, 
       if (!*abort) i = (long long)atomicAdd(ticket, 1ull);
       s_op = i;
       s_ok = i >= 0 && i < nops;
+      if (s_ok && trace) {
+        trace[i].t_take = global_ns();
+        trace[i].cta = (uint32_t)blockIdx.x;
+      }
     }
     __syncthreads();
     if (!s_ok) return;
@@ -387,6 +392,7 @@ __global__ void __launch_bounds__(256) k_flow(const FlowOp* flow, int64_t nops, 
         __nanosleep(20);
       }
       __threadfence();
+      if (trace) trace[s_op].t_ready = global_ns();
       s_go = ok;  // not s_ok: another thread may still be reading it
     }
     __syncthreads();
@@ -404,14 +410,22 @@ __global__ void __launch_bounds__(256) k_flow(const FlowOp* flow, int64_t nops, 
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();  // the op's writes before its signals
-      for (int64_t e = succ_off[s_op]; e < succ_off[s_op + 1]; ++e) atomicAdd(count + succ[e], 1);
+      if (trace) {
+        trace[s_op].t_done = global_ns();
+        for (int64_t e = succ_off[s_op]; e < succ_off[s_op + 1]; ++e) {
+          const int32_t v = succ[e];
+          if (atomicAdd(count + v, 1) + 1 == npred[v]) trace[v].releaser = (int32_t)s_op;
+        }
+      } else {
+        for (int64_t e = succ_off[s_op]; e < succ_off[s_op + 1]; ++e) atomicAdd(count + succ[e], 1);
+      }
     }
   }
 }
 
 int launch_flow(const FlowOp* flow, int64_t nops, const int32_t* npred, const int64_t* succ_off, const int32_t* succ,
                 int32_t* count, const OpTrsm* trsm, const OpGemm* gemm, const Bases& B, GridBar* gb, int max_dense,
-                int per_sm, cudaStream_t st) {
+                int per_sm, FactorTrace* trace, cudaStream_t st) {
   int maxper = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&maxper, k_flow, 256, trsm_smem(max_dense)) != cudaSuccess)
     return -1;
@@ -424,7 +438,7 @@ int launch_flow(const FlowOp* flow, int64_t nops, const int32_t* npred, const in
   if (cudaMemsetAsync(gb, 0, sizeof(GridBar), st) != cudaSuccess) return -1;
   if (cudaMemsetAsync(count, 0, nops * sizeof(int32_t), st) != cudaSuccess) return -1;
   void* args[] = {(void*)&flow, (void*)&nops, (void*)&npred, (void*)&succ_off, (void*)&succ, (void*)&count,
-                  (void*)&trsm, (void*)&gemm, (void*)&B, (void*)&gb};
+                  (void*)&trsm, (void*)&gemm, (void*)&B, (void*)&gb, (void*)&trace};
   return cudaLaunchCooperativeKernel((void*)k_flow, grid, 256, args, trsm_smem(max_dense), st) == cudaSuccess ? 0
                                                                                                                : -1;
 }

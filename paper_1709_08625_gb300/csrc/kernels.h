@@ -37,7 +37,7 @@ int launch_factor(const Plan& P, const Bases& B, GridBar* gb, int max_dense, Fac
                   cudaStream_t st);
 int launch_flow(const FlowOp* flow, int64_t nops, const int32_t* npred, const int64_t* succ_off, const int32_t* succ,
                 int32_t* count, const OpTrsm* trsm, const OpGemm* gemm, const Bases& B, GridBar* gb, int max_dense,
-                int per_sm, cudaStream_t st);
+                int per_sm, FactorTrace* trace, cudaStream_t st);
 // Two CTAs wait at a grid barrier that expects one arrival more than the
 // grid has; the wait ends by its time limit with DEV_TIMEOUT in *status.
 int launch_barrier_probe(GridBar* gb, int* status, cudaStream_t st);
