@@ -53,10 +53,16 @@ def run(n0=524288, n=65536, seed=0, true=(1.0, 0.0864, 0.5), nugget=1e-4, start=
         r, tr = tree.fit(z, st, trace_cap=4 * max_iter + 16 if trace else 0, max_iter=max_iter,
                          size_tol=size_tol)
         t_fit = time.perf_counter() - t0
+        # the likelihood at the true theta, for comparison with the maximum
+        # found (on a ridge of nearly equal likelihood, sigma2 / ell^(2 nu)
+        # is what the data fix best)
+        l_true = tree.loglik(hlc.theta(s2, ell, nu, nugget), z)["loglik"]
         out = dict(n0=n0, n=n, seed=seed, eps=eps, leaf=leaf, precision=precision,
                    gen_precision=gen_precision or precision, nugget=nugget,
                    true=dict(sigma2=s2, ell=ell, nu=nu), start=dict(sigma2=start[0], ell=start[1], nu=start[2]),
-                   estimate=dict(sigma2=r["sigma2"], ell=r["ell"], nu=r["nu"]), loglik_start=l_start, fit=r,
+                   estimate=dict(sigma2=r["sigma2"], ell=r["ell"], nu=r["nu"]), loglik_start=l_start,
+                   loglik_true=l_true, fit=r,
+                   microergodic=dict(true=s2 / ell ** (2 * nu), estimate=r["sigma2"] / r["ell"] ** (2 * r["nu"])),
                    seconds_generate=t_gen, seconds_fit=t_fit,
                    ms_per_eval=r["ms_total"] / max(r["evaluations"], 1))
         if trace:
