@@ -176,6 +176,11 @@ int upload_plan(Plan& P) {
   if ((st = upload(&P.d_succ, P.succ))) return st;
   if (!P.flow.empty()) CK(cudaMalloc(&P.d_count, P.flow.size() * sizeof(int32_t)));
   if (P.ngroups > 0) CK(cudaMalloc(&P.d_groups, P.ngroups * sizeof(TrGroup)));
+  // the ready queue serves the factorisation (the plan with truncations)
+  if (!P.flow.empty() && !P.trunc.empty()) {
+    if ((st = upload(&P.d_ready0, P.ready0))) return st;
+    CK(cudaMalloc(&P.d_ready, P.flow.size() * sizeof(int32_t)));
+  }
   if ((st = upload(&P.d_chain, P.chain))) return st;
   if ((st = upload(&P.d_citems, P.citems))) return st;
   if ((st = upload(&P.d_ctrsm, P.ctrsm))) return st;
@@ -199,6 +204,10 @@ void free_plan(Plan& P) {
   cudaFree(P.d_succ);
   cudaFree(P.d_count);
   cudaFree(P.d_groups);
+  cudaFree(P.d_ready0);
+  cudaFree(P.d_ready);
+  P.d_ready0 = nullptr;
+  P.d_ready = nullptr;
   P.d_groups = nullptr;
   P.d_flow = nullptr;
   P.d_npred = nullptr;

@@ -1203,9 +1203,10 @@ struct Planner {
 
   // Dataflow form of a plan: the ops in wave order (flow), the number of
   // predecessors of each and its successors (CSR).  A group truncation
-  // (OP_TRUNC_BIG) becomes kGroupParts consecutive entries: every part waits
-  // for the op's producers, and part 0 alone signals the op's consumers
-  // (after the group's last barrier, when every part is done).
+  // (OP_TRUNC_BIG) becomes kGroupParts consecutive entries: the op's
+  // producers count towards part 0 only, all parts become ready together,
+  // and part 0 alone signals the op's consumers (after the group's last
+  // barrier, when every part is done).
   static constexpr int kGroupParts = 8;
   void build_flow(const std::vector<int64_t>& order) {
     P.flow.clear();
@@ -1226,16 +1227,17 @@ struct Planner {
       const int64_t grp = np > 1 ? P.ngroups++ : -1;
       for (int p = 0; p < np; ++p) P.flow.push_back(FlowOp{r.type, p, idx, grp});
     }
+    // a group's producers signal its first part only; the parts become ready
+    // together (the kernel queues all of them when the first is released)
     const int64_t F = (int64_t)P.flow.size();
     std::vector<int64_t> nsucc(F, 0);
     P.npred.assign(F, 0);
     for (int64_t q = 0; q < N; ++q) {
       if (q >= (int64_t)preds.size()) continue;
-      for (int64_t d : preds[q])
-        for (int64_t p = 0; p < parts_of[q]; ++p) {
-          P.npred[pos_of[q] + p] += 1;
-          nsucc[pos_of[d]] += 1;
-        }
+      for (int64_t d : preds[q]) {
+        P.npred[pos_of[q]] += 1;
+        nsucc[pos_of[d]] += 1;
+      }
     }
     P.succ_off.assign(F + 1, 0);
     for (int64_t i = 0; i < F; ++i) P.succ_off[i + 1] = P.succ_off[i] + nsucc[i];
@@ -1243,8 +1245,14 @@ struct Planner {
     std::vector<int64_t> fill(P.succ_off.begin(), P.succ_off.end() - 1);
     for (int64_t q = 0; q < N; ++q) {
       if (q >= (int64_t)preds.size()) continue;
-      for (int64_t d : preds[q])
-        for (int64_t p = 0; p < parts_of[q]; ++p) P.succ[fill[pos_of[d]]++] = (int32_t)(pos_of[q] + p);
+      for (int64_t d : preds[q]) P.succ[fill[pos_of[d]]++] = (int32_t)pos_of[q];
+    }
+    // the ops ready at the start, in flow order (a group with all its parts)
+    P.ready0.clear();
+    for (int64_t q = 0; q < N; ++q) {
+      const int64_t f = pos_of[order[q]];
+      if (P.npred[f] != 0) continue;
+      for (int64_t p = 0; p < parts_of[order[q]]; ++p) P.ready0.push_back((int32_t)(f + p));
     }
   }
 };

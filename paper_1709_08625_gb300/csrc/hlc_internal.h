@@ -192,7 +192,8 @@ struct Launch {
 // State of the persistent kernel's grid barrier (zeroed before each launch).
 struct GridBar {
   unsigned int count, gen, abort, pad;
-  unsigned long long ticket;  // next op number of the dataflow kernel
+  unsigned long long ticket;  // next op number (solves) or ready-queue slot (factorisation) to take
+  unsigned long long tail;    // ready-queue slots filled beyond the initially ready ops
 };
 
 // TRSM, GEMM and chain op ranges of one wave (persistent execution of a
@@ -248,11 +249,16 @@ struct Plan {
   std::vector<int32_t> npred;
   std::vector<int64_t> succ_off;
   std::vector<int32_t> succ;
+  // the ops without producers, in flow order (a group with all its parts):
+  // the first entries of the factorisation's ready queue
+  std::vector<int32_t> ready0;
   FlowOp* d_flow = nullptr;
   int32_t* d_npred = nullptr;
   int64_t* d_succ_off = nullptr;
   int32_t* d_succ = nullptr;
   int32_t* d_count = nullptr;  // arrivals per op (zeroed before each run)
+  int32_t* d_ready0 = nullptr; // device copy of ready0
+  int32_t* d_ready = nullptr;  // ready queue of the factorisation (one slot per op)
   int64_t ngroups = 0;         // group truncations (OP_TRUNC_BIG) of a dataflow factorisation
   TrGroup* d_groups = nullptr;
   int64_t tmp_doubles = 0;

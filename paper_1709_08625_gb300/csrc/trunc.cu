@@ -58,6 +58,12 @@ struct TrCh {
   static constexpr int value = sizeof(T) == 8 ? 32 : 64;  // rows at K = TR_KT
   static constexpr int elems = value * TR_KT;
 };
+// the core's work arrays reuse the chunk buffer (free between the QR and
+// the apply): its size in entries of the core type
+template <class T, class C>
+__host__ __device__ constexpr int64_t core_smem_elems() {
+  return (int64_t)TrCh<T>::elems * (int64_t)sizeof(T) / (int64_t)sizeof(C);
+}
 constexpr int TR_THREADS = 256;
 constexpr int TR_CL = 8;       // CTAs per cluster for large targets
 constexpr int64_t TR_REG = (int64_t)TR_KT * TR_KT;
@@ -323,10 +329,21 @@ __device__ __forceinline__ void phase_mark(unsigned long long* ph, int slot, lon
   }
 }
 
+// Work arrays, all with leading dimension K: M (K x K), and once the
+// numerical rank r of M is known W (K x r), J and X (r x r, in K x r
+// regions).  They live in the shared buffer sm (sm_elems entries of the core
+// type) as far as they fit -- M when K^2 <= sm_elems, the others when
+// K^2 + 3 K r <= sm_elems as well -- and otherwise in the CTA's scratch scr.
+// Cu, Cv: K x k outputs in the scratch (leading dimension TR_KT); Ru, Rv:
+// the R factors (TR_KT).
 template <class T, class C>
-__device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, int kfix, C* M, C* W, C* J, C* X, C* Cu,
-                        C* Cv, CoreShared<C>& cs, int* status,
+__device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, int kfix, C* sm, int64_t sm_elems,
+                        double* scr, C* Cu, C* Cv, CoreShared<C>& cs, int* status,
                         unsigned long long* ph = nullptr) {
+  constexpr int ldc = TR_KT;
+  const int ld = K;
+  C* M = (int64_t)K * K <= sm_elems ? sm : reinterpret_cast<C*>(scr + 2 * TR_REG);
+  C *W, *J, *X;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
   long long t0 = clock64();
   // M = Ru Rv^T (both upper triangular)
@@ -334,7 +351,7 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, i
     const int i = e % K, j = e / K;
     C s = C(0);
     for (int c = max(i, j); c < K; ++c) s += (C)Ru[i + (int64_t)c * TR_KT] * (C)Rv[j + (int64_t)c * TR_KT];
-    M[i + (int64_t)j * TR_KT] = s;
+    M[i + (int64_t)j * ld] = s;
   }
   for (int j = tid; j < K; j += blockDim.x) cs.piv[j] = j;
   __syncthreads();
@@ -355,7 +372,7 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, i
   C* cn1 = cs.cn2;
   for (int j = w; j < K; j += nw) {
     C p = C(0);
-    for (int i = lane; i < K; i += 32) p += M[i + (int64_t)j * TR_KT] * M[i + (int64_t)j * TR_KT];
+    for (int i = lane; i < K; i += 32) p += M[i + (int64_t)j * ld] * M[i + (int64_t)j * ld];
     p = warp_sum(p);
     if (lane == 0) cn0[j] = p;
   }
@@ -386,9 +403,9 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, i
     if (ref == C(0) || !(sqrt(rem) > stop_rel * ref)) break;
     if (jm != r) {
       for (int i = tid; i < K; i += blockDim.x) {
-        const C a = M[i + (int64_t)r * TR_KT];
-        M[i + (int64_t)r * TR_KT] = M[i + (int64_t)jm * TR_KT];
-        M[i + (int64_t)jm * TR_KT] = a;
+        const C a = M[i + (int64_t)r * ld];
+        M[i + (int64_t)r * ld] = M[i + (int64_t)jm * ld];
+        M[i + (int64_t)jm * ld] = a;
       }
       if (tid == 0) {
         const int t = cs.piv[r];
@@ -398,9 +415,9 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, i
     }
     __syncthreads();
     C xn = C(0);
-    for (int i = r + 1 + lane; i < K; i += 32) xn += M[i + (int64_t)r * TR_KT] * M[i + (int64_t)r * TR_KT];
+    for (int i = r + 1 + lane; i < K; i += 32) xn += M[i + (int64_t)r * ld] * M[i + (int64_t)r * ld];
     xn = warp_sum(xn);
-    const C alpha = M[r + (int64_t)r * TR_KT];
+    const C alpha = M[r + (int64_t)r * ld];
     C tau = C(0), sc = C(1), beta = alpha;
     if (xn > C(0)) {
       beta = -copysign(sqrt(alpha * alpha + xn), alpha);
@@ -414,18 +431,18 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, i
     }
     for (int l = r + 1 + w; l < K; l += nw) {
       C p = C(0);
-      for (int i = r + 1 + lane; i < K; i += 32) p += M[i + (int64_t)r * TR_KT] * M[i + (int64_t)l * TR_KT];
+      for (int i = r + 1 + lane; i < K; i += 32) p += M[i + (int64_t)r * ld] * M[i + (int64_t)l * ld];
       p = warp_sum(p);
-      const C wv = tau * (M[r + (int64_t)l * TR_KT] + sc * p), ws = wv * sc;
+      const C wv = tau * (M[r + (int64_t)l * ld] + sc * p), ws = wv * sc;
       C q = C(0);
       for (int i = r + 1 + lane; i < K; i += 32) {
-        const C v = M[i + (int64_t)l * TR_KT] - ws * M[i + (int64_t)r * TR_KT];
-        M[i + (int64_t)l * TR_KT] = v;
+        const C v = M[i + (int64_t)l * ld] - ws * M[i + (int64_t)r * ld];
+        M[i + (int64_t)l * ld] = v;
         q += v * v;
       }
       q = warp_sum(q);
       if (lane == 0) {
-        M[r + (int64_t)l * TR_KT] -= wv;
+        M[r + (int64_t)l * ld] -= wv;
         nxt[l] = q;
       }
     }
@@ -435,13 +452,21 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, i
   for (int e = tid; e < r * K; e += blockDim.x) {
     const int q = e / K, i = e % K;
     if (i == q)
-      M[q + (int64_t)q * TR_KT] = cs.sv[q];
+      M[q + (int64_t)q * ld] = cs.sv[q];
     else if (i > q && cs.tauq[q] != C(0))
-      M[i + (int64_t)q * TR_KT] *= cs.scl[q];
+      M[i + (int64_t)q * ld] *= cs.scl[q];
   }
   __syncthreads();
   const int rank = r;
-  (void)X;
+  if (M == sm && (int64_t)K * K + 3 * (int64_t)K * rank <= sm_elems) {
+    W = M + (int64_t)K * K;
+    J = W + (int64_t)K * rank;
+    X = J + (int64_t)K * rank;
+  } else {
+    W = reinterpret_cast<C*>(scr + 3 * TR_REG);
+    J = reinterpret_cast<C*>(scr + 4 * TR_REG);
+    X = reinterpret_cast<C*>(scr + TR_OFF_X);
+  }
   phase_mark(ph, 4, t0);
   if (ph && tid == 0) atomicAdd(ph + 10, (unsigned long long)rank);
   if (rank == 0) {
@@ -452,7 +477,7 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, i
   // B = (R P^T)^T (K x rank) into W
   for (int e = tid; e < K * rank; e += blockDim.x) {
     const int j = e % K, i = e / K;  // R(i, j) -> B(piv[j], i)
-    W[cs.piv[j] + (int64_t)i * TR_KT] = (i <= j) ? M[i + (int64_t)j * TR_KT] : C(0);
+    W[cs.piv[j] + (int64_t)i * ld] = (i <= j) ? M[i + (int64_t)j * ld] : C(0);
   }
   __syncthreads();
   // Householder QR of B (K x rank): B = Q_B R_B; the one-sided Jacobi then
@@ -461,9 +486,9 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, i
   for (int q = 0; q < rank; ++q) {
     if (w == 0) {
       C xn = C(0);
-      for (int i = q + 1 + lane; i < K; i += 32) xn += W[i + (int64_t)q * TR_KT] * W[i + (int64_t)q * TR_KT];
+      for (int i = q + 1 + lane; i < K; i += 32) xn += W[i + (int64_t)q * ld] * W[i + (int64_t)q * ld];
       xn = warp_sum(xn);
-      const C alpha = W[q + (int64_t)q * TR_KT];
+      const C alpha = W[q + (int64_t)q * ld];
       C tau = C(0), sc = C(0), beta = alpha;
       if (xn > C(0)) {
         beta = -copysign(sqrt(alpha * alpha + xn), alpha);
@@ -471,9 +496,9 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, i
         sc = C(1) / (alpha - beta);
       }
       if (tau != C(0))
-        for (int i = q + 1 + lane; i < K; i += 32) W[i + (int64_t)q * TR_KT] *= sc;
+        for (int i = q + 1 + lane; i < K; i += 32) W[i + (int64_t)q * ld] *= sc;
       if (lane == 0) {
-        W[q + (int64_t)q * TR_KT] = beta;
+        W[q + (int64_t)q * ld] = beta;
         cs.cn[q] = tau;  // tau of the B reflectors
       }
     }
@@ -482,11 +507,11 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, i
     if (tau != C(0)) {
       for (int l = q + 1 + w; l < rank; l += nw) {
         C p = C(0);
-        for (int i = q + 1 + lane; i < K; i += 32) p += W[i + (int64_t)q * TR_KT] * W[i + (int64_t)l * TR_KT];
+        for (int i = q + 1 + lane; i < K; i += 32) p += W[i + (int64_t)q * ld] * W[i + (int64_t)l * ld];
         p = warp_sum(p);
-        const C wv = tau * (p + W[q + (int64_t)l * TR_KT]);
-        for (int i = q + 1 + lane; i < K; i += 32) W[i + (int64_t)l * TR_KT] -= wv * W[i + (int64_t)q * TR_KT];
-        if (lane == 0) W[q + (int64_t)l * TR_KT] -= wv;
+        const C wv = tau * (p + W[q + (int64_t)l * ld]);
+        for (int i = q + 1 + lane; i < K; i += 32) W[i + (int64_t)l * ld] -= wv * W[i + (int64_t)q * ld];
+        if (lane == 0) W[q + (int64_t)l * ld] -= wv;
       }
     }
     __syncthreads();
@@ -497,14 +522,14 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, i
   C* A = X;
   for (int e = tid; e < rank * rank; e += blockDim.x) {
     const int i = e % rank, j = e / rank;
-    A[i + (int64_t)j * TR_KT] = (i >= j) ? W[j + (int64_t)i * TR_KT] : C(0);
-    J[i + (int64_t)j * TR_KT] = (i == j) ? C(1) : C(0);
+    A[i + (int64_t)j * ld] = (i >= j) ? W[j + (int64_t)i * ld] : C(0);
+    J[i + (int64_t)j * ld] = (i == j) ? C(1) : C(0);
   }
   __syncthreads();
   // one-sided Jacobi on the rank columns of A, round-robin pairs
   C fro2 = C(0);
   for (int e = tid; e < rank * rank; e += blockDim.x) {
-    const C v = A[(e % rank) + (int64_t)(e / rank) * TR_KT];
+    const C v = A[(e % rank) + (int64_t)(e / rank) * ld];
     fro2 += v * v;
   }
   fro2 = block_sum(fro2, cs.red + 1);
@@ -533,7 +558,7 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, i
         if (b >= rank) continue;
         C al = C(0), be = C(0), ga = C(0);
         for (int i = lane; i < rank; i += 32) {
-          const C x = A[i + (int64_t)a * TR_KT], y = A[i + (int64_t)b * TR_KT];
+          const C x = A[i + (int64_t)a * ld], y = A[i + (int64_t)b * ld];
           al += x * x;
           be += y * y;
           ga += x * y;
@@ -547,12 +572,12 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, i
         const C t = (zeta >= C(0) ? C(1) : C(-1)) / (fabs(zeta) + sqrt(C(1) + zeta * zeta));
         const C c = C(1) / sqrt(C(1) + t * t), sn = c * t;
         for (int i = lane; i < rank; i += 32) {
-          const C x = A[i + (int64_t)a * TR_KT], y = A[i + (int64_t)b * TR_KT];
-          A[i + (int64_t)a * TR_KT] = c * x - sn * y;
-          A[i + (int64_t)b * TR_KT] = sn * x + c * y;
-          const C jx = J[i + (int64_t)a * TR_KT], jy = J[i + (int64_t)b * TR_KT];
-          J[i + (int64_t)a * TR_KT] = c * jx - sn * jy;
-          J[i + (int64_t)b * TR_KT] = sn * jx + c * jy;
+          const C x = A[i + (int64_t)a * ld], y = A[i + (int64_t)b * ld];
+          A[i + (int64_t)a * ld] = c * x - sn * y;
+          A[i + (int64_t)b * ld] = sn * x + c * y;
+          const C jx = J[i + (int64_t)a * ld], jy = J[i + (int64_t)b * ld];
+          J[i + (int64_t)a * ld] = c * jx - sn * jy;
+          J[i + (int64_t)b * ld] = sn * jx + c * jy;
         }
         if (lane == 0) cs.rot = 1;
       }
@@ -565,7 +590,7 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, i
   // singular values, order (ties: smaller index first), truncation rank
   for (int j = w; j < rank; j += nw) {
     C s = C(0);
-    for (int i = lane; i < rank; i += 32) s += A[i + (int64_t)j * TR_KT] * A[i + (int64_t)j * TR_KT];
+    for (int i = lane; i < rank; i += 32) s += A[i + (int64_t)j * ld] * A[i + (int64_t)j * ld];
     s = warp_sum(s);
     if (lane == 0) cs.sv[j] = sqrt(s);
   }
@@ -605,25 +630,25 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, i
   for (int c = w; c < k; c += nw) {
     const int j = cs.order[c];
     const C sv = cs.sv[j];
-    C* x = Cv + (int64_t)c * TR_KT;
-    C* y = Cu + (int64_t)c * TR_KT;
+    C* x = Cv + (int64_t)c * ldc;
+    C* y = Cu + (int64_t)c * ldc;
     for (int i = lane; i < K; i += 32) {
-      x[i] = i < rank ? A[i + (int64_t)j * TR_KT] / sv : C(0);
-      y[i] = i < rank ? J[i + (int64_t)j * TR_KT] : C(0);
+      x[i] = i < rank ? A[i + (int64_t)j * ld] / sv : C(0);
+      y[i] = i < rank ? J[i + (int64_t)j * ld] : C(0);
     }
     __syncwarp();
     for (int q = rank - 1; q >= 0; --q) {
       const C tq = cs.tauq[q], tb = cs.cn[q];
       C p = C(0), pb = C(0);
       for (int i = q + lane; i < K; i += 32) {
-        p += (i == q ? C(1) : M[i + (int64_t)q * TR_KT]) * x[i];
-        pb += (i == q ? C(1) : W[i + (int64_t)q * TR_KT]) * y[i];
+        p += (i == q ? C(1) : M[i + (int64_t)q * ld]) * x[i];
+        pb += (i == q ? C(1) : W[i + (int64_t)q * ld]) * y[i];
       }
       p = warp_sum(p);
       pb = warp_sum(pb);
       for (int i = q + lane; i < K; i += 32) {
-        if (tq != C(0)) x[i] -= tq * p * (i == q ? C(1) : M[i + (int64_t)q * TR_KT]);
-        if (tb != C(0)) y[i] -= tb * pb * (i == q ? C(1) : W[i + (int64_t)q * TR_KT]);
+        if (tq != C(0)) x[i] -= tq * p * (i == q ? C(1) : M[i + (int64_t)q * ld]);
+        if (tb != C(0)) y[i] -= tb * pb * (i == q ? C(1) : W[i + (int64_t)q * ld]);
       }
       __syncwarp();
     }
@@ -639,11 +664,11 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, i
   for (int e = tid; e < k * k; e += blockDim.x) {
     const int i = e % k, j = e / k;
     if (i < j) continue;
-    const C* xi = Cv + (int64_t)i * TR_KT;
-    const C* xj = Cv + (int64_t)j * TR_KT;
+    const C* xi = Cv + (int64_t)i * ldc;
+    const C* xj = Cv + (int64_t)j * ldc;
     C g = C(0);
     for (int q = 0; q < K; ++q) g += xi[q] * xj[q];
-    G[i + (int64_t)j * TR_KT] = g;
+    G[i + (int64_t)j * ld] = g;
   }
   __syncthreads();
   // G = L L^T in place (warp 0, left-looking); G is near the identity, so a
@@ -653,18 +678,18 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, i
     int ok = 1;
     for (int j = 0; j < k; ++j) {
       C part = C(0);
-      for (int q = lane; q < j; q += 32) part += G[j + (int64_t)q * TR_KT] * G[j + (int64_t)q * TR_KT];
+      for (int q = lane; q < j; q += 32) part += G[j + (int64_t)q * ld] * G[j + (int64_t)q * ld];
       part = warp_sum(part);
-      const C d = G[j + (int64_t)j * TR_KT] - part;
+      const C d = G[j + (int64_t)j * ld] - part;
       if (!(d > C(0.25))) ok = 0;
       const C ljj = sqrt(d > C(0.25) ? d : C(1));
       for (int i = j + 1 + lane; i < k; i += 32) {
-        C g = G[i + (int64_t)j * TR_KT];
-        for (int q = 0; q < j; ++q) g -= G[i + (int64_t)q * TR_KT] * G[j + (int64_t)q * TR_KT];
-        G[i + (int64_t)j * TR_KT] = g / ljj;
+        C g = G[i + (int64_t)j * ld];
+        for (int q = 0; q < j; ++q) g -= G[i + (int64_t)q * ld] * G[j + (int64_t)q * ld];
+        G[i + (int64_t)j * ld] = g / ljj;
       }
       __syncwarp();
-      if (lane == 0) G[j + (int64_t)j * TR_KT] = ljj;
+      if (lane == 0) G[j + (int64_t)j * ld] = ljj;
       __syncwarp();
     }
     if (lane == 0) cs.rot = ok;
@@ -674,15 +699,15 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, i
   for (int e = tid; e < K * k; e += blockDim.x) {
     const int col = e % K, c = e / K;
     const C isq = C(1) / sqrt(cs.sv[cs.order[c]]);
-    const C* y = Cu + (int64_t)c * TR_KT;
-    const C* x = Cv + (int64_t)c * TR_KT;
+    const C* y = Cu + (int64_t)c * ldc;
+    const C* x = Cv + (int64_t)c * ldc;
     C a = C(0), b = C(0);
     for (int q = 0; q <= col; ++q) {
       a += (C)Rv[q + (int64_t)col * TR_KT] * y[q];
       b += (C)Ru[q + (int64_t)col * TR_KT] * x[q];
     }
-    W[col + (int64_t)c * TR_KT] = a * isq;
-    M[col + (int64_t)c * TR_KT] = b;
+    W[col + (int64_t)c * ld] = a * isq;
+    M[col + (int64_t)c * ld] = b;
   }
   __syncthreads();
   // each row of R_u^T X_k times G^-1 (one thread per row), then S^-1/2
@@ -690,14 +715,14 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, i
     for (int col = tid; col < K; col += blockDim.x) {
       C* row = M + col;
       for (int c = 0; c < k; ++c) {
-        C v = row[(int64_t)c * TR_KT];
-        for (int q = 0; q < c; ++q) v -= G[c + (int64_t)q * TR_KT] * row[(int64_t)q * TR_KT];
-        row[(int64_t)c * TR_KT] = v / G[c + (int64_t)c * TR_KT];
+        C v = row[(int64_t)c * ld];
+        for (int q = 0; q < c; ++q) v -= G[c + (int64_t)q * ld] * row[(int64_t)q * ld];
+        row[(int64_t)c * ld] = v / G[c + (int64_t)c * ld];
       }
       for (int c = k - 1; c >= 0; --c) {
-        C v = row[(int64_t)c * TR_KT];
-        for (int q = c + 1; q < k; ++q) v -= G[q + (int64_t)c * TR_KT] * row[(int64_t)q * TR_KT];
-        row[(int64_t)c * TR_KT] = v / G[c + (int64_t)c * TR_KT];
+        C v = row[(int64_t)c * ld];
+        for (int q = c + 1; q < k; ++q) v -= G[q + (int64_t)c * ld] * row[(int64_t)q * ld];
+        row[(int64_t)c * ld] = v / G[c + (int64_t)c * ld];
       }
     }
   }
@@ -705,8 +730,8 @@ __device__ void tr_core(const T* Ru, const T* Rv, int K, double eps, int kcap, i
   for (int e = tid; e < K * k; e += blockDim.x) {
     const int col = e % K, c = e / K;
     const C isq = C(1) / sqrt(cs.sv[cs.order[c]]);
-    Cu[col + (int64_t)c * TR_KT] = W[col + (int64_t)c * TR_KT];
-    Cv[col + (int64_t)c * TR_KT] = M[col + (int64_t)c * TR_KT] * isq;
+    Cu[col + (int64_t)c * ldc] = W[col + (int64_t)c * ld];
+    Cv[col + (int64_t)c * ldc] = M[col + (int64_t)c * ld] * isq;
   }
   __syncthreads();
   phase_mark(ph, 6, t0);
@@ -787,10 +812,6 @@ __device__ void trunc_one(const OpTrunc& op, const TermD* terms, const Bases& B,
   double* sh = ts.sh;
   T* Pu = reinterpret_cast<T*>(scr);
   T* Pv = reinterpret_cast<T*>(scr + TR_REG);
-  C* M = reinterpret_cast<C*>(scr + 2 * TR_REG);
-  C* W = reinterpret_cast<C*>(scr + 3 * TR_REG);
-  C* J = reinterpret_cast<C*>(scr + 4 * TR_REG);
-  C* X = reinterpret_cast<C*>(scr + TR_OFF_X);
   C* Cu = reinterpret_cast<C*>(scr + TR_OFF_CU);
   C* Cv = reinterpret_cast<C*>(scr + TR_OFF_CV);
   const TermD* tl = terms + op.term0;
@@ -826,7 +847,8 @@ __device__ void trunc_one(const OpTrunc& op, const TermD* terms, const Bases& B,
       qr_stream<T>([&](int r, int c) { return cat_value(B, op, cat, 1, r, c); }, op.n, K, Pv, sC, sh);
     }
     phase_mark(B.phase, 2, tp);
-    tr_core<T, C>(Pu, Pv, K, op.eps, op.kcap, op.kfix, M, W, J, X, Cu, Cv, cs, B.status, B.phase);
+    tr_core<T, C>(Pu, Pv, K, op.eps, op.kcap, op.kfix, reinterpret_cast<C*>(sC), core_smem_elems<T, C>(), scr, Cu,
+                  Cv, cs, B.status, B.phase);
     tp = clock64();
     const int k = cs.k;
     // algorithmic flops of the batch: two streamed R factors and the apply
@@ -867,10 +889,7 @@ __device__ void trunc_part(const OpTrunc& op, const TermD* terms, const Bases& B
   double* scr = scr_of(rk);
   T* Pu = reinterpret_cast<T*>(scr);
   T* Pv = reinterpret_cast<T*>(scr + TR_REG);
-  C* M = reinterpret_cast<C*>(scr + 2 * TR_REG);
-  C* W = reinterpret_cast<C*>(scr + 3 * TR_REG);
-  C* J = reinterpret_cast<C*>(scr + 4 * TR_REG);
-  C* X = reinterpret_cast<C*>(scr + TR_OFF_X);
+  C* J = reinterpret_cast<C*>(scr + 4 * TR_REG);  // the combined R factor of this part's side
   C* Cu0 = reinterpret_cast<C*>(scr_of(0) + TR_OFF_CU);  // coefficients live with part 0
   C* Cv0 = reinterpret_cast<C*>(scr_of(0) + TR_OFF_CV);
   int* flag0 = reinterpret_cast<int*>(scr_of(0) + TR_OFF_FLAG);
@@ -930,7 +949,8 @@ __device__ void trunc_part(const OpTrunc& op, const TermD* terms, const Bases& B
         Rv[i + (int64_t)j * TR_KT] = fv[i + (int64_t)j * TR_KT];
       }
       __syncthreads();
-      tr_core<T, C>(Ru, Rv, K, op.eps, op.kcap, op.kfix, M, W, J, X, Cu0, Cv0, cs, B.status);
+      tr_core<T, C>(Ru, Rv, K, op.eps, op.kcap, op.kfix, reinterpret_cast<C*>(sC), core_smem_elems<T, C>(), scr,
+                    Cu0, Cv0, cs, B.status);
       if (threadIdx.x == 0) flag0[0] = cs.k;
     }
     if (!sync()) return;
@@ -971,29 +991,32 @@ __global__ void __cluster_dims__(TR_CL, 1, 1) __launch_bounds__(TR_THREADS, size
 
 // ---------------------------------------------------------------------------
 // The whole H-Cholesky as one dependency-driven cooperative launch.  The ops
-// of the plan (POTRF, TRSM, GEMM, truncations) are numbered in wave order;
-// each CTA takes the next number from a ticket counter, waits until every
-// producer of that op has signalled, runs it and signals its consumers.  A
-// group truncation is TR_CL consecutive numbers, one per part: its CTAs meet
-// at the start (each publishes its scratch slice) and at every phase of the
-// op through bounded barriers in global memory, and part 0 signals the
-// consumers when all parts are done.  Progress: tickets go out in wave order
-// and producers always have smaller numbers, so the unfinished op with the
-// smallest number either runs (a single-CTA op: its producers are done) or
-// is a group whose remaining parts are the very next tickets, which the next
-// CTAs to finish take (the grid has more than TR_CL CTAs).  Every wait is
+// of the plan (POTRF, TRSM, GEMM, truncations) run in the order they become
+// ready: a ready queue holds one slot per op, its first n0 slots the ops
+// without producers; a free CTA takes the next slot number from a counter,
+// waits until that slot is filled, runs the op and signals its consumers; the
+// CTA whose signal completes a consumer's count appends the consumer to the
+// queue.  A group truncation is TR_CL consecutive ops, one per part, queued
+// together in TR_CL consecutive slots when its first part is released: its
+// CTAs meet at the start (each publishes its scratch slice) and at every
+// phase of the op through bounded barriers in global memory, and part 0
+// signals the consumers when all parts are done.  Progress: every queued op
+// can run (its producers are done), a group's parts are taken by the next
+// TR_CL free CTAs (the grid has more than TR_CL CTAs), and every op is
+// queued once its producers finish, so every slot is filled.  Every wait is
 // bounded (kBarrierNs): a CTA that gives up records DEV_TIMEOUT and raises
 // the abort flag, and every CTA leaves.  Each op computes what it computes in
 // the wave launches, after the same producers: the results are the waves'.
-// With a trace buffer (FactorTrace per op) the kernel records when each op
-// was taken, became ready and finished, its CTA, and the producer whose
-// signal released it.
+// With a trace buffer (FactorTrace per op) the kernel records when a CTA
+// took the op's slot, when the slot was filled and when the op finished, its
+// CTA, and the producer whose signal released it.
 // ---------------------------------------------------------------------------
 template <class T, class C>
 __global__ void __launch_bounds__(TR_THREADS, sizeof(T) == 4 ? 2 : 1)
     k_factor(const FlowOp* flow, int64_t nops, const int32_t* npred, const int64_t* succ_off, const int32_t* succ,
-             int32_t* count, const OpPotrf* potrf, const OpTrsm* trsm, const OpGemm* gemm, const OpTrunc* trunc,
-             const TermD* terms, TrGroup* groups, Bases B, GridBar* gb, FactorTrace* trace) {
+             int32_t* count, int32_t* ready, int64_t n0, const OpPotrf* potrf, const OpTrsm* trsm,
+             const OpGemm* gemm, const OpTrunc* trunc, const TermD* terms, TrGroup* groups, Bases B, GridBar* gb,
+             FactorTrace* trace) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ TrShared<C> ts;
   __shared__ GemmSmem<T> gs;
@@ -1003,18 +1026,13 @@ __global__ void __launch_bounds__(TR_THREADS, sizeof(T) == 4 ? 2 : 1)
   for (;;) {
     if (threadIdx.x == 0) {
       volatile unsigned int* abort = &gb->abort;
-      long long i = -1;
-      if (!*abort) i = (long long)atomicAdd(&gb->ticket, 1ull);
-      int ok = i >= 0 && i < nops;
-      if (ok && trace) {
-        trace[i].t_take = global_ns();
-        trace[i].cta = (uint32_t)blockIdx.x;
-      }
+      long long slot = -1, i = -1;
+      if (!*abort) slot = (long long)atomicAdd(&gb->ticket, 1ull);
+      int ok = slot >= 0 && slot < nops;
       if (ok) {
-        const volatile int32_t* cnt = count + i;
-        const int32_t need = npred[i];
         const unsigned long long t0 = global_ns();
-        while (*cnt < need) {
+        const volatile int32_t* q = ready + slot;
+        while ((i = *q) < 0) {
           if (*abort || global_ns() - t0 > kBarrierNs) {
             atomicExch(&gb->abort, 1u);
             record_error(B.status, DEV_TIMEOUT, 2);
@@ -1024,7 +1042,11 @@ __global__ void __launch_bounds__(TR_THREADS, sizeof(T) == 4 ? 2 : 1)
           __nanosleep(20);
         }
         __threadfence();
-        if (trace) trace[i].t_ready = global_ns();
+        if (ok && trace) {
+          trace[i].t_take = t0;
+          trace[i].t_ready = global_ns();
+          trace[i].cta = (uint32_t)blockIdx.x;
+        }
       }
       s_op = i;
       s_ok = ok;
@@ -1066,14 +1088,15 @@ __global__ void __launch_bounds__(TR_THREADS, sizeof(T) == 4 ? 2 : 1)
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();  // the op's writes before its signals
-      if (trace) {
-        trace[s_op].t_done = global_ns();
-        for (int64_t e = succ_off[s_op]; e < succ_off[s_op + 1]; ++e) {
-          const int32_t v = succ[e];
-          if (atomicAdd(count + v, 1) + 1 == npred[v]) trace[v].releaser = (int32_t)s_op;
-        }
-      } else {
-        for (int64_t e = succ_off[s_op]; e < succ_off[s_op + 1]; ++e) atomicAdd(count + succ[e], 1);
+      if (trace) trace[s_op].t_done = global_ns();
+      for (int64_t e = succ_off[s_op]; e < succ_off[s_op + 1]; ++e) {
+        const int32_t v = succ[e];
+        if (atomicAdd(count + v, 1) + 1 != npred[v]) continue;
+        // the last producer of v: queue it (a group with all its parts)
+        const int np = flow[v].type == OP_TRUNC_BIG ? TR_CL : 1;
+        const long long pos = n0 + (long long)atomicAdd(&gb->tail, (unsigned long long)np);
+        if (trace) trace[v].releaser = (int32_t)s_op;
+        for (int p = 0; p < np; ++p) atomicExch(ready + pos + p, v + p);
       }
     }
   }
@@ -1145,11 +1168,18 @@ static int launch_factor_t(const Plan& P, const Bases& B, GridBar* gb, int max_d
   if (cudaMemsetAsync(gb, 0, sizeof(GridBar), st) != cudaSuccess) return -1;
   if (cudaMemsetAsync(P.d_count, 0, nops * sizeof(int32_t), st) != cudaSuccess) return -1;
   if (P.ngroups && cudaMemsetAsync(P.d_groups, 0, P.ngroups * sizeof(TrGroup), st) != cudaSuccess) return -1;
+  // the ready queue: the ops without producers, then empty slots (-1)
+  const int64_t n0 = (int64_t)P.ready0.size();
+  if (!P.d_ready || !P.d_ready0 || n0 <= 0) return -1;
+  if (cudaMemsetAsync(P.d_ready, 0xff, nops * sizeof(int32_t), st) != cudaSuccess) return -1;
+  if (cudaMemcpyAsync(P.d_ready, P.d_ready0, n0 * sizeof(int32_t), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return -1;
   const FlowOp* flow = P.d_flow;
   const int32_t* npred = P.d_npred;
   const int64_t* so = P.d_succ_off;
   const int32_t* sc = P.d_succ;
   int32_t* cnt = P.d_count;
+  int32_t* rq = P.d_ready;
   const OpPotrf* po = P.d_potrf;
   const OpTrsm* tr = P.d_trsm;
   const OpGemm* ge = P.d_gemm;
@@ -1157,8 +1187,9 @@ static int launch_factor_t(const Plan& P, const Bases& B, GridBar* gb, int max_d
   const TermD* te = P.d_terms;
   TrGroup* gr = P.d_groups;
   Bases b = B;
-  void* args[] = {(void*)&flow, (void*)&nops, (void*)&npred, (void*)&so, (void*)&sc, (void*)&cnt, (void*)&po,
-                  (void*)&tr, (void*)&ge, (void*)&tu, (void*)&te, (void*)&gr, (void*)&b, (void*)&gb, (void*)&trace};
+  void* args[] = {(void*)&flow, (void*)&nops, (void*)&npred, (void*)&so,  (void*)&sc, (void*)&cnt,
+                  (void*)&rq,   (void*)&n0,   (void*)&po,    (void*)&tr,  (void*)&ge, (void*)&tu,
+                  (void*)&te,   (void*)&gr,   (void*)&b,     (void*)&gb,  (void*)&trace};
   return cudaLaunchCooperativeKernel((void*)k_factor<T, C>, grid, TR_THREADS, args, sm, st) == cudaSuccess ? 0 : -1;
 }
 
