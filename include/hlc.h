@@ -52,8 +52,9 @@
  *                     result, bit for bit)
  *   HLC_PROFILE=1     time every op launch (synchronising) and print a summary
  *                     at exit
- *   HLC_PHASES=1      count clock cycles per phase of the truncation kernel and
- *                     print them when the context is destroyed
+ *   HLC_PHASES=1      count clock cycles per phase of the truncation kernel
+ *                     (separately for batches of at most 32 columns and wider
+ *                     ones) and print them when the context is destroyed
  *   HLC_FACTOR_TRACE=<path>  record the dependency-driven factorisation's
  *                     timeline (per op: taken, ready, done, CTA, releasing
  *                     producer) and write it to <path> after every

@@ -1022,8 +1022,8 @@ int hlc_create(hlc_ctx** out, int device) {
   if (e == cudaSuccess) e = cudaMalloc(&c->d_flops, NOPTYPES * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(c->d_flops, 0, NOPTYPES * sizeof(double));
   if (e == cudaSuccess && getenv("HLC_PHASES") && getenv("HLC_PHASES")[0] == '1') {
-    e = cudaMalloc(&c->d_phase, 16 * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMemset(c->d_phase, 0, 16 * sizeof(unsigned long long));
+    e = cudaMalloc(&c->d_phase, 32 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(c->d_phase, 0, 32 * sizeof(unsigned long long));
   }
   if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, 16);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_gridbar, sizeof(GridBar));
@@ -1062,17 +1062,22 @@ void hlc_destroy(hlc_ctx* c) {
   cudaFree(c->d_scratch);
   cudaFree(c->d_flops);
   if (c->d_phase) {
-    unsigned long long ph[16];
-    if (cudaMemcpy(ph, c->d_phase, sizeof(ph), cudaMemcpyDeviceToHost) == cudaSuccess && ph[11]) {
-      static const char* nm[8] = {"", "qr U", "qr V", "core M", "core QRCP", "core QR+Jacobi", "core vectors",
-                                  "apply"};
-      double tot = 0;
-      for (int i = 1; i < 8; ++i) tot += (double)ph[i];
-      fprintf(stderr, "hlc-phases batches %llu  mean K %.1f  mean rank %.1f\n", ph[11], (double)ph[12] / ph[11],
-              (double)ph[10] / ph[11]);
-      for (int i = 1; i < 8; ++i)
-        fprintf(stderr, "hlc-phases %-16s %14.0f cycles (%5.1f %%) %10.1f per batch\n", nm[i], (double)ph[i],
-                100.0 * ph[i] / tot, (double)ph[i] / ph[11]);
+    // two sets of counters: batches of K <= 32 columns, and wider ones
+    unsigned long long all[32];
+    if (cudaMemcpy(all, c->d_phase, sizeof(all), cudaMemcpyDeviceToHost) == cudaSuccess) {
+      for (int set = 0; set < 2; ++set) {
+        const unsigned long long* ph = all + 16 * set;
+        if (!ph[11]) continue;
+        static const char* nm[8] = {"", "qr U", "qr V", "core M", "core QRCP", "core QR+Jacobi", "core vectors",
+                                    "apply"};
+        double tot = 0;
+        for (int i = 1; i < 8; ++i) tot += (double)ph[i];
+        fprintf(stderr, "hlc-phases %s batches %llu  mean K %.1f  mean rank %.1f\n", set ? "K > 32" : "K <= 32",
+                ph[11], (double)ph[12] / ph[11], (double)ph[10] / ph[11]);
+        for (int i = 1; i < 8; ++i)
+          fprintf(stderr, "hlc-phases %-16s %14.0f cycles (%5.1f %%) %10.1f per batch\n", nm[i], (double)ph[i],
+                  100.0 * ph[i] / tot, (double)ph[i] / ph[11]);
+      }
     }
     cudaFree(c->d_phase);
   }

@@ -1207,6 +1207,13 @@ struct Planner {
   // producers count towards part 0 only, all parts become ready together,
   // and part 0 alone signals the op's consumers (after the group's last
   // barrier, when every part is done).
+  //
+  // In a solve, a one-column product whose only consumer is the TRSM of the
+  // same rows (the update of a diagonal block's right-hand side by its
+  // neighbour, then its substitution) joins that TRSM: the TRSM's flow entry
+  // names the product (FlowOp::group), which the same CTA runs first, and the
+  // product's producers become the TRSM's.  One dependency hop less per
+  // diagonal block; each op computes what it computes alone.
   static constexpr int kGroupParts = 8;
   void build_flow(const std::vector<int64_t>& order) {
     P.flow.clear();
@@ -1215,17 +1222,60 @@ struct Planner {
     P.succ.clear();
     P.ngroups = 0;
     const int64_t N = (int64_t)order.size();
-    std::vector<int64_t> pos_of(N), parts_of(N);  // seq index -> first flow index, parts
-    std::vector<int64_t> cnt_t(NOPTYPES, 0);
+    // final array index of every op (the arrays are in wave order)
+    std::vector<int64_t> aidx(N);
+    {
+      std::vector<int64_t> cnt_t(NOPTYPES, 0);
+      for (int64_t i = 0; i < N; ++i) {
+        const Ref& r = seq[order[i]];
+        const int32_t arr = r.type == OP_TRUNC_BIG ? OP_TRUNC : r.type;  // both truncation kinds share one array
+        aidx[order[i]] = cnt_t[arr]++;
+      }
+    }
+    std::vector<int64_t> joined_into(N, -1);  // product -> the TRSM it joins
+    std::vector<int64_t> pre_of(N, -1);       // TRSM -> the product it runs first
+    if (P.trunc.empty()) {
+      std::vector<int32_t> nsucc_op(N, 0);
+      for (int64_t q = 0; q < (int64_t)preds.size(); ++q)
+        for (int64_t d : preds[q]) nsucc_op[d] += 1;
+      for (int64_t q = 0; q < (int64_t)preds.size(); ++q) {
+        if (seq[q].type != OP_TRSM) continue;
+        const OpTrsm& t = P.trsm[aidx[q]];
+        for (int64_t d : preds[q]) {
+          if (seq[d].type != OP_GEMM || nsucc_op[d] != 1 || joined_into[d] >= 0) continue;
+          const OpGemm& g = P.gemm[aidx[d]];
+          const bool one_col = g.c.slot < 0 && g.c.n == 1 && t.c.slot < 0 && t.c.n == 1;
+          const bool same_rows = g.Y.buf == t.X.buf && g.Y.off == t.X.off && g.Y.rs == t.X.rs && g.m.slot < 0 &&
+                                 g.m.n == t.n;
+          const bool matrix_a = (g.A.buf == BUF_L || g.A.buf == BUF_C) && g.B.buf >= 0;
+          if (one_col && same_rows && matrix_a) {
+            joined_into[d] = q;
+            pre_of[q] = d;
+            break;
+          }
+        }
+      }
+    }
+    std::vector<int64_t> pos_of(N, -1), parts_of(N, 0);  // seq index -> first flow index, parts
     for (int64_t i = 0; i < N; ++i) {
-      const Ref& r = seq[order[i]];
-      pos_of[order[i]] = (int64_t)P.flow.size();
+      const int64_t q = order[i];
+      if (joined_into[q] >= 0) continue;
+      const Ref& r = seq[q];
+      pos_of[q] = (int64_t)P.flow.size();
       const int np = r.type == OP_TRUNC_BIG ? kGroupParts : 1;
-      parts_of[order[i]] = np;
-      const int32_t arr = r.type == OP_TRUNC_BIG ? OP_TRUNC : r.type;  // both truncation kinds share one array
-      const int64_t idx = cnt_t[arr]++;
-      const int64_t grp = np > 1 ? P.ngroups++ : -1;
-      for (int p = 0; p < np; ++p) P.flow.push_back(FlowOp{r.type, p, idx, grp});
+      parts_of[q] = np;
+      const int64_t grp = np > 1 ? P.ngroups++ : (pre_of[q] >= 0 ? aidx[pre_of[q]] : -1);
+      for (int p = 0; p < np; ++p) P.flow.push_back(FlowOp{r.type, p, aidx[q], grp});
+    }
+    // the producers of a joined product become its TRSM's
+    for (int64_t q = 0; q < N; ++q) {
+      if (pre_of[q] < 0 || pre_of[q] >= (int64_t)preds.size()) continue;
+      std::vector<int64_t>& d = preds[q];
+      d.erase(std::remove(d.begin(), d.end(), pre_of[q]), d.end());
+      d.insert(d.end(), preds[pre_of[q]].begin(), preds[pre_of[q]].end());
+      std::sort(d.begin(), d.end());
+      d.erase(std::unique(d.begin(), d.end()), d.end());
+      preds[pre_of[q]].clear();
     }
     // a group's producers signal its first part only; the parts become ready
     // together (the kernel queues all of them when the first is released)
@@ -1233,7 +1283,7 @@ struct Planner {
     std::vector<int64_t> nsucc(F, 0);
     P.npred.assign(F, 0);
     for (int64_t q = 0; q < N; ++q) {
-      if (q >= (int64_t)preds.size()) continue;
+      if (q >= (int64_t)preds.size() || pos_of[q] < 0) continue;
       for (int64_t d : preds[q]) {
         P.npred[pos_of[q]] += 1;
         nsucc[pos_of[d]] += 1;
@@ -1244,14 +1294,14 @@ struct Planner {
     P.succ.assign(P.succ_off[F], 0);
     std::vector<int64_t> fill(P.succ_off.begin(), P.succ_off.end() - 1);
     for (int64_t q = 0; q < N; ++q) {
-      if (q >= (int64_t)preds.size()) continue;
+      if (q >= (int64_t)preds.size() || pos_of[q] < 0) continue;
       for (int64_t d : preds[q]) P.succ[fill[pos_of[d]]++] = (int32_t)pos_of[q];
     }
     // the ops ready at the start, in flow order (a group with all its parts)
     P.ready0.clear();
     for (int64_t q = 0; q < N; ++q) {
       const int64_t f = pos_of[order[q]];
-      if (P.npred[f] != 0) continue;
+      if (f < 0 || P.npred[f] != 0) continue;
       for (int64_t p = 0; p < parts_of[order[q]]; ++p) P.ready0.push_back((int32_t)(f + p));
     }
   }

@@ -206,7 +206,9 @@ struct WaveRange {
 
 // An op of a dataflow plan: its type and index in that type's array.  A
 // truncation run by a group of CTAs (OP_TRUNC_BIG) has one entry per part
-// (part 0..parts-1, consecutive), sharing the group record `group`.
+// (part 0..parts-1, consecutive), sharing the group record `group`.  For a
+// TRSM of a dataflow solve, `group` is the GEMM (a one-column product into
+// the TRSM's rows) that the same CTA runs first, or -1.
 struct FlowOp {
   int32_t type;
   int32_t part;

@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(256) k_waves(const WaveRange* waves, int nwave
 __global__ void __launch_bounds__(256) k_flow(const FlowOp* flow, int64_t nops, const int32_t* npred,
                                               const int64_t* succ_off, const int32_t* succ, int32_t* count,
                                               const OpTrsm* trsm, const OpGemm* gemm, Bases B, GridBar* gb,
-                                              FactorTrace* trace) {
+                                              FactorTrace* trace, int64_t smem_entries) {
   extern __shared__ double sL[];
   __shared__ GemmSmem<double> gd;
   __shared__ GemmSmem<float> gf;
@@ -368,12 +368,24 @@ __global__ void __launch_bounds__(256) k_flow(const FlowOp* flow, int64_t nops, 
     __syncthreads();
     if (!s_ok) return;
     const FlowOp f = flow[s_op];
-    // a solve's factor block is final: load it while the producers finish
+    // a solve's factor block (a matvec's block of C~) is final: load it while
+    // the producers finish
+    bool pre = false;
+    const OpGemm* g = f.type == OP_GEMM ? gemm + f.idx : f.group >= 0 ? gemm + f.group : nullptr;
     if (f.type == OP_TRSM) {
-      if (B.mixed)
+      // the block, then (when it fits beside it) the joined product's operand
+      const int64_t used = (int64_t)trsm[f.idx].n * trsm[f.idx].n + trsm[f.idx].n;
+      if (B.mixed) {
         trsm_load<float>(trsm[f.idx], B, reinterpret_cast<float*>(sL));
-      else
+        if (g) pre = gemv_prefetch<float>(*g, B, reinterpret_cast<float*>(sL) + used, 2 * smem_entries - used);
+      } else {
         trsm_load<double>(trsm[f.idx], B, sL);
+        if (g) pre = gemv_prefetch<double>(*g, B, sL + used, smem_entries - used);
+      }
+    } else if (B.mixed) {
+      pre = gemv_prefetch<float>(gemm[f.idx], B, reinterpret_cast<float*>(sL), 2 * smem_entries);
+    } else {
+      pre = gemv_prefetch<double>(gemm[f.idx], B, sL, smem_entries);
     }
     if (threadIdx.x == 0) {
       // wait for the producers of the op
@@ -398,10 +410,27 @@ __global__ void __launch_bounds__(256) k_flow(const FlowOp* flow, int64_t nops, 
     __syncthreads();
     if (!s_go) return;
     if (f.type == OP_TRSM) {
+      const int64_t used = (int64_t)trsm[f.idx].n * trsm[f.idx].n + trsm[f.idx].n;
+      if (g) {  // the joined product first: it writes the rows the TRSM reads
+        if (pre && B.mixed)
+          do_gemv_pre<float>(*g, B, reinterpret_cast<const float*>(sL) + used);
+        else if (pre)
+          do_gemv_pre<double>(*g, B, sL + used);
+        else if (B.mixed)
+          do_gemm<float>(*g, B, gf);
+        else
+          do_gemm<double>(*g, B, gd);
+        __syncthreads();
+      }
       if (B.mixed)
         trsm_apply<float>(trsm[f.idx], B, reinterpret_cast<const float*>(sL));
       else
         trsm_apply<double>(trsm[f.idx], B, sL);
+    } else if (pre) {
+      if (B.mixed)
+        do_gemv_pre<float>(gemm[f.idx], B, reinterpret_cast<const float*>(sL));
+      else
+        do_gemv_pre<double>(gemm[f.idx], B, sL);
     } else if (B.mixed) {
       do_gemm<float>(gemm[f.idx], B, gf);
     } else {
@@ -437,8 +466,9 @@ int launch_flow(const FlowOp* flow, int64_t nops, const int32_t* npred, const in
   if (grid <= 0 || nops <= 0 || !gb || !count) return -1;
   if (cudaMemsetAsync(gb, 0, sizeof(GridBar), st) != cudaSuccess) return -1;
   if (cudaMemsetAsync(count, 0, nops * sizeof(int32_t), st) != cudaSuccess) return -1;
+  int64_t sent = (int64_t)(trsm_smem(max_dense) / sizeof(double));  // dynamic shared memory in doubles
   void* args[] = {(void*)&flow, (void*)&nops, (void*)&npred, (void*)&succ_off, (void*)&succ, (void*)&count,
-                  (void*)&trsm, (void*)&gemm, (void*)&B, (void*)&gb, (void*)&trace};
+                  (void*)&trsm, (void*)&gemm, (void*)&B, (void*)&gb, (void*)&trace, (void*)&sent};
   return cudaLaunchCooperativeKernel((void*)k_flow, grid, 256, args, trsm_smem(max_dense), st) == cudaSuccess ? 0
                                                                                                                : -1;
 }

@@ -277,6 +277,104 @@ __device__ void do_gemv(const OpGemm& op, const Bases& B, int m, int k, double* 
   if (P > 1) __syncthreads();
 }
 
+// Prefetch for the dependency-driven solves: the A operand of a product
+// with one column (a block of the factor or of C~, final while a solve or
+// matvec runs) into shared memory as T, sA[i + q m], before the op's
+// producers are done.  Returns whether it did (m k <= cap entries, A in a
+// matrix arena); the CTA then runs do_gemv_pre after the wait, which adds
+// in exactly do_gemv's order.
+template <class T>
+__device__ bool gemv_prefetch(const OpGemm& op, const Bases& B, T* sA, int64_t cap) {
+  if (op.B.buf == MV_IDENTITY || (op.A.buf != BUF_L && op.A.buf != BUF_C)) return false;
+  const int m = dimv(op.m, B.ranks), k = dimv(op.k, B.ranks), c = dimv(op.c, B.ranks);
+  if (m <= 0 || k <= 0 || (c != 1 && op.B.buf != MV_ONES) || (int64_t)m * k > cap) return false;
+  const double* A = vptr(B, op.A);
+  const int n = m * k;
+  for (int e0 = threadIdx.x; e0 < n; e0 += LD_BATCH * blockDim.x) {
+    T v[LD_BATCH];
+#pragma unroll
+    for (int u = 0; u < LD_BATCH; ++u) {
+      const int e = e0 + u * blockDim.x;
+      v[u] = e < n ? (T)A[(int64_t)(e % m) * op.A.rs + (int64_t)(e / m) * op.A.cs] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < LD_BATCH; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e < n) sA[e] = v[u];
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
+// do_gemv with A prefetched (gemv_prefetch): the same threads add the same
+// products in the same order.
+template <class T>
+__device__ void do_gemv_pre(const OpGemm& op, const Bases& B, const T* sA) {
+  __shared__ T gp_red[256];
+  const int m = dimv(op.m, B.ranks), k = dimv(op.k, B.ranks);
+  if (B.flops && threadIdx.x == 0) atomicAdd(B.flops + OP_GEMM, 2.0 * m * (double)k);
+  double* Y = vptr(B, op.Y);
+  const bool ones = op.B.buf == MV_ONES;
+  const double* x = ones ? nullptr : vptr(B, op.B);
+  const int64_t xs = op.B.rs;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
+  if (op.A.cs == 1 && op.A.rs != 1) {
+    for (int i = w; i < m; i += nw) {
+      T acc = T(0);
+      if (ones)
+        for (int q = lane; q < k; q += 32) acc += sA[i + q * m];
+      else
+        for (int q = lane; q < k; q += 32) acc += sA[i + q * m] * (T)x[q * xs];
+      acc = warp_sum(acc);
+      if (lane == 0) {
+        double* yp = Y + (int64_t)i * op.Y.rs;
+        const double v = op.alpha * (double)acc;
+        *yp = op.beta ? *yp + v : v;
+      }
+    }
+    __syncthreads();
+    return;
+  }
+  const int nt = (int)blockDim.x;
+  const int R = min(nt, (m + 31) & ~31);
+  const int P = nt / R;
+  const int r = tid % R, p = tid / R;
+  for (int r0 = 0; r0 < m; r0 += R) {
+    const int i = r0 + r;
+    T acc = T(0);
+    if (i < m && p < P) {
+      for (int q0 = p; q0 < k; q0 += GV_UNROLL * P) {
+        T av[GV_UNROLL], xv[GV_UNROLL];
+#pragma unroll
+        for (int u = 0; u < GV_UNROLL; ++u) {
+          const int q = q0 + u * P;
+          av[u] = q < k ? sA[i + q * m] : T(0);
+          xv[u] = q < k ? (ones ? T(1) : (T)x[(int64_t)q * xs]) : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < GV_UNROLL; ++u) acc += av[u] * xv[u];
+      }
+    }
+    if (P > 1) {
+      __syncthreads();
+      if (p < P) gp_red[p * R + r] = acc;
+      __syncthreads();
+      if (p == 0 && i < m) {
+        T s = T(0);
+        for (int q = 0; q < P; ++q) s += gp_red[q * R + r];
+        acc = s;
+      }
+    }
+    if (p == 0 && i < m) {
+      double* yp = Y + (int64_t)i * op.Y.rs;
+      const double v = op.alpha * (double)acc;
+      *yp = op.beta ? *yp + v : v;
+    }
+  }
+  __syncthreads();
+}
+
 template <class T>
 __device__ void do_gemm(const OpGemm& op, const Bases& B, GemmSmem<T>& sm) {
   const int tid = threadIdx.x, tr = tid & 15, tc = tid >> 4;

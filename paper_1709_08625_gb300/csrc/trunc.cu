@@ -833,22 +833,24 @@ __device__ void trunc_one(const OpTrunc& op, const TermD* terms, const Bases& B,
       break;
     }
     long long tp = clock64();
-    if (B.phase && threadIdx.x == 0) {
-      atomicAdd(B.phase + 11, 1ull);
-      atomicAdd(B.phase + 12, (unsigned long long)K);
+    // phase counters (HLC_PHASES): one set for K <= 32, one for wider batches
+    unsigned long long* ph = B.phase ? B.phase + (K > 32 ? 16 : 0) : nullptr;
+    if (ph && threadIdx.x == 0) {
+      atomicAdd(ph + 11, 1ull);
+      atomicAdd(ph + 12, (unsigned long long)K);
     }
     if (K <= 32) {
       qr_tsqr_pair<T>([&](int r, int c) { return cat_value(B, op, cat, 0, r, c); }, op.m,
                       [&](int r, int c) { return cat_value(B, op, cat, 1, r, c); }, op.n, K, Pu, Pv, sC);
-      phase_mark(B.phase, 1, tp);
+      phase_mark(ph, 1, tp);
     } else {
       qr_stream<T>([&](int r, int c) { return cat_value(B, op, cat, 0, r, c); }, op.m, K, Pu, sC, sh);
-      phase_mark(B.phase, 1, tp);
+      phase_mark(ph, 1, tp);
       qr_stream<T>([&](int r, int c) { return cat_value(B, op, cat, 1, r, c); }, op.n, K, Pv, sC, sh);
     }
-    phase_mark(B.phase, 2, tp);
+    phase_mark(ph, 2, tp);
     tr_core<T, C>(Pu, Pv, K, op.eps, op.kcap, op.kfix, reinterpret_cast<C*>(sC), core_smem_elems<T, C>(), scr, Cu,
-                  Cv, cs, B.status, B.phase);
+                  Cv, cs, B.status, ph);
     tp = clock64();
     const int k = cs.k;
     // algorithmic flops of the batch: two streamed R factors and the apply
@@ -856,7 +858,7 @@ __device__ void trunc_one(const OpTrunc& op, const TermD* terms, const Bases& B,
       atomicAdd(B.flops + OP_TRUNC, 2.0 * K * K * (double)(op.m + op.n) + 2.0 * K * (double)k * (op.m + op.n));
     tr_apply<T, C>(B, op, cat, 0, 0, op.m, K, k, Cu, sC);
     tr_apply<T, C>(B, op, cat, 1, 0, op.n, K, k, Cv, sC);
-    phase_mark(B.phase, 7, tp);
+    phase_mark(ph, 7, tp);
     kacc = k;
     __syncthreads();
   }
