@@ -34,6 +34,14 @@ WORKLOAD = "n524288_nu0.5_eps1e-5"
 SAMPLE_N = 32768  # oracle sample: the first SAMPLE_N locations of the workload (~Table 5's smallest n)
 FP32_LANES_PER_SM = 128
 NUM_SMS = 152
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_factor
+# launch of the mixed-precision workload, from one ncu capture of the kernel
+# as it is now (one pass, the first of the two factorisations):
+#   python -m paper_1709_08625_gb300.compare_precisions --precisions mixed n524288_nu0.5_eps1e-5 &&
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none -k regex:k_factor -c 1 \
+#       python -m paper_1709_08625_gb300.compare_precisions --precisions mixed n524288_nu0.5_eps1e-5
+# None where no capture of the current kernel exists.
+K_FACTOR_TRAFFIC = {"n524288_nu0.5_eps1e-5": None}
 
 
 def parse():
@@ -404,7 +412,8 @@ def run_ours(args, rank, ws, local, dist):
                     "steps": e2e_steps},
             "gpu_launches": int(cnt["launches"]),
             "roofline": {"bound": "alu", "kernel": factor_kernel, "achieved": achieved, "peak": peak, "unit": unit,
-                         "frac": achieved / peak if peak else None, "traffic": None,
+                         "frac": achieved / peak if peak else None,
+                         "traffic": K_FACTOR_TRAFFIC.get(args.workload) if args.precision == "mixed" else None,
                          "launch_ms": factor_ms, "launch_gflop": factor_flops / 1e9,
                          "note": "one H-Cholesky at the workload: algorithmic flops counted by its ops (POTRF "
                                  "n^3/3, TRSM n^2 c, GEMM 2mkc, truncation 2K^2(m+n) + 2Kk(m+n) per batch) over "

@@ -115,12 +115,28 @@ __device__ __forceinline__ double cat_value(const Bases& B, const OpTrunc& op, c
 }
 
 // Streaming Householder QR: R (K x K, ld TR_KT, type T) of the nrows x K
-// matrix whose entries rowval(i, c) returns.  sC: TrCh<T> x K chunk buffer.
+// matrix whose entries rowval(i, c) returns; buf: the TrCh<T> chunk buffer.
+// Row chunks are folded into R one at a time ([R; chunk] -> R).  Step j
+// reflects column j of [R; chunk]: the reflector is (1 at row j of R;
+// sc x_j on the chunk), and since Q is never formed the chunk column x_j is
+// left unscaled (sc is folded into the updates).  Every warp computes the
+// step's scalars itself from R(j, j) and the squared norm of x_j, which the
+// warp that updated column j in the previous step left in shared memory
+// (look-ahead), so a step takes one block barrier.  R stays in shared memory
+// while it leaves room for a 32-row chunk, and is copied out at the end.
 template <class T, class F>
-__device__ void qr_stream(F rowval, int nrows, int K, T* R, T* sC, double* sh) {
-  const int TR_CH = max(32, (TrCh<T>::elems / max(K, 1)) & ~31);
+__device__ void qr_stream(F rowval, int nrows, int K, T* Rout, T* buf, double* sh) {
+  (void)sh;
+  __shared__ T s_xn[2];
+  constexpr int64_t E = TrCh<T>::elems;
+  const bool rsm = (int64_t)K * K + 32LL * K <= E;
+  T* R = rsm ? buf : Rout;
+  const int ldr = rsm ? K : TR_KT;
+  T* sC = rsm ? buf + (int64_t)K * K : buf;
+  const int64_t cap = rsm ? E - (int64_t)K * K : E;
+  const int TR_CH = max(32, (int)((cap / max(K, 1)) & ~31));
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
-  for (int e = tid; e < K * K; e += blockDim.x) R[(e % K) + (int64_t)(e / K) * TR_KT] = T(0);
+  for (int e = tid; e < K * K; e += blockDim.x) R[(e % K) + (int64_t)(e / K) * ldr] = T(0);
   __syncthreads();
   for (int r0 = 0; r0 < nrows; r0 += TR_CH) {
     const int rows = min(TR_CH, nrows - r0);
@@ -129,39 +145,61 @@ __device__ void qr_stream(F rowval, int nrows, int K, T* R, T* sC, double* sh) {
       sC[i + c * TR_CH] = (T)rowval(r0 + i, c);
     }
     __syncthreads();
-    for (int j = 0; j < K; ++j) {
-      if (w == 0) {
-        T xn = T(0);
-        for (int i = lane; i < rows; i += 32) xn += sC[i + j * TR_CH] * sC[i + j * TR_CH];
-        for (int o = 16; o > 0; o >>= 1) xn += __shfl_xor_sync(0xffffffffu, xn, o);
-        const T alpha = R[j + (int64_t)j * TR_KT];
-        T tau = T(0), sc = T(0), beta = alpha;
-        if (xn > T(0)) {
-          beta = -copysign(sqrt(alpha * alpha + xn), alpha);
-          tau = (beta - alpha) / beta;
-          sc = T(1) / (alpha - beta);
-        }
-        if (tau != T(0))
-          for (int i = lane; i < rows; i += 32) sC[i + j * TR_CH] *= sc;
-        if (lane == 0) {
-          R[j + (int64_t)j * TR_KT] = beta;
-          sh[0] = (double)tau;
-        }
-      }
-      __syncthreads();
-      const T tau = (T)sh[0];
-      if (tau != T(0)) {
-        for (int l = j + 1 + w; l < K; l += nw) {
-          T p = T(0);
-          for (int i = lane; i < rows; i += 32) p += sC[i + j * TR_CH] * sC[i + l * TR_CH];
-          for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
-          const T wv = tau * (p + R[j + (int64_t)l * TR_KT]);
-          for (int i = lane; i < rows; i += 32) sC[i + l * TR_CH] -= wv * sC[i + j * TR_CH];
-          if (lane == 0) R[j + (int64_t)l * TR_KT] -= wv;
-        }
-      }
-      __syncthreads();
+    if (w == 0) {
+      T xn = T(0);
+      for (int i = lane; i < rows; i += 32) xn += sC[i] * sC[i];
+      xn = warp_sum(xn);
+      if (lane == 0) s_xn[0] = xn;
     }
+    __syncthreads();
+    for (int j = 0; j < K; ++j) {
+      const T xn = s_xn[j & 1];
+      const T alpha = R[j + (int64_t)j * ldr];
+      T tau = T(0), sc = T(0), beta = alpha;
+      if (xn > T(0)) {
+        beta = -copysign(sqrt(alpha * alpha + xn), alpha);
+        tau = (beta - alpha) / beta;
+        sc = T(1) / (alpha - beta);
+      }
+      const T* xj = sC + j * TR_CH;
+      for (int l = j + 1 + w; l < K; l += nw) {
+        T* xl = sC + l * TR_CH;
+        if (tau != T(0)) {
+          T p = T(0);
+          for (int i = lane; i < rows; i += 32) p += xj[i] * xl[i];
+          p = warp_sum(p);
+          const T rjl = R[j + (int64_t)l * ldr];
+          const T wv = tau * (rjl + sc * p), ws = wv * sc;
+          T q = T(0);
+          for (int i = lane; i < rows; i += 32) {
+            const T v = xl[i] - ws * xj[i];
+            xl[i] = v;
+            q += v * v;
+          }
+          if (l == j + 1) {
+            q = warp_sum(q);
+            if (lane == 0) s_xn[(j + 1) & 1] = q;
+          }
+          __syncwarp();
+          if (lane == 0) R[j + (int64_t)l * ldr] = rjl - wv;
+        } else if (l == j + 1) {
+          T q = T(0);
+          for (int i = lane; i < rows; i += 32) q += xl[i] * xl[i];
+          q = warp_sum(q);
+          if (lane == 0) s_xn[(j + 1) & 1] = q;
+        }
+      }
+      __syncthreads();
+      if (tid == 0) R[j + (int64_t)j * ldr] = beta;
+    }
+    __syncthreads();
+  }
+  if (rsm) {
+    for (int e = tid; e < K * K; e += blockDim.x) {
+      const int i = e % K, c = e / K;
+      Rout[i + (int64_t)c * TR_KT] = R[i + (int64_t)c * K];
+    }
+    __syncthreads();
   }
 }
 
