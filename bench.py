@@ -41,7 +41,7 @@ NUM_SMS = 152
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none -k regex:k_factor -c 1 \
 #       python -m paper_1709_08625_gb300.compare_precisions --precisions mixed n524288_nu0.5_eps1e-5
 # None where no capture of the current kernel exists.
-K_FACTOR_TRAFFIC = {"n524288_nu0.5_eps1e-5": None}
+K_FACTOR_TRAFFIC = {"n524288_nu0.5_eps1e-5": 144.41e9 + 156.48e9}
 
 
 def parse():
