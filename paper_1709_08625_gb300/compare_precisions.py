@@ -41,12 +41,12 @@ def run(names, precisions=("mixed", "fp64"), device=0, first=0):
                                      kmax=128 if w["nu"] > 1 else 64)
                     try:
                         t.loglik(th, z)
-                        first = time.perf_counter() - t0
+                        first_s = time.perf_counter() - t0
                         r = t.loglik(th, z)
                     finally:
                         t.free()
                     res[pn] = {k: r[k] for k in KEYS}
-                    res[pn]["first_call_s"] = first
+                    res[pn]["first_call_s"] = first_s
                 except hlc.HlcError as e:
                     res[pn] = {"err": str(e)}
             if "loglik" in res.get("mixed", {}) and "loglik" in res.get("fp64", {}):
