@@ -287,6 +287,26 @@ int64_t hlc_matvec_noalloc_capacity(void);
  */
 int hlc_selftest_barrier_timeout(hlc_ctx* ctx);
 
+/*
+ * Host-only self-test of the planner's dataflow programs (no device, no
+ * context; no counterpart in the paper).  Builds a synthetic cluster tree
+ * (midpoint bisection of the index interval [0, n) down to `leaf` points)
+ * and block-cluster tree (admissible iff min(size) <= eta * index gap), the
+ * H-Cholesky (a7), forward and backward solve (a9, a10) and matvec plans at
+ * rank capacity kmax, and checks what the dependency-driven kernels rely on:
+ * plans inside their buffers, dependency edges pointing forward, predecessor
+ * counts, group truncations as consecutive parts with edges on the first,
+ * the ready list, products joined into TRSMs, and a model run of the
+ * factorisation kernel's ready-queue protocol with `ctas` CTAs (> 8) and
+ * op durations drawn from `seed`.  stats (up to 12 entries): factorisation
+ * ops, edges, groups, initially ready ops; forward ops, joined products;
+ * backward ops, joined products; matvec ops; model makespan; leaves; rank
+ * slots.  Returns HLC_OK, HLC_ERR_STATE with the first violation in msg
+ * (msglen bytes, NUL-terminated), HLC_ERR_ARG or HLC_ERR_OOM.
+ */
+int hlc_selftest_plans(int64_t n, int leaf, double eta, int kmax, int ctas, uint64_t seed, int64_t* stats,
+                       int nstats, char* msg, int msglen);
+
 /* Dense expansion of C~ (symmetric) or L~ (lower) into an n x n column-major
  * host array in caller order; for small n only (n <= 16384). */
 int hlc_hmat_expand(hlc_ctx* ctx, const hlc_hmat* M, double* out);

@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "libhlc.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off", "-I" + CSRC]
-SOURCES = ["kernels.cu", "trunc.cu", "tree.cu", "api.cu", "serve.cu", "engine.cpp", "fit.cpp"]
+SOURCES = ["kernels.cu", "trunc.cu", "tree.cu", "api.cu", "serve.cu", "engine.cpp", "fit.cpp", "selftest.cpp"]
 
 
 def _newest_input() -> float:
