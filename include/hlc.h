@@ -290,22 +290,25 @@ int hlc_selftest_barrier_timeout(hlc_ctx* ctx);
 /*
  * Host-only self-test of the planner's dataflow programs (no device, no
  * context; no counterpart in the paper).  Builds a synthetic cluster tree
- * (midpoint bisection of the index interval [0, n) down to `leaf` points)
- * and block-cluster tree (admissible iff min(size) <= eta * index gap), the
+ * (midpoint bisection of the index interval [0, n) down to `leaf` points;
+ * boxes: geometry 0 the intervals themselves, geometry 1 the tight boxes of
+ * a square grid's points numbered in Morton order, n <= 2^26) and
+ * block-cluster tree (admissible iff min(diam) <= eta * dist), the
  * H-Cholesky (a7), forward and backward solve (a9, a10) and matvec plans at
  * rank capacity kmax, and checks what the dependency-driven kernels rely on:
  * plans inside their buffers, dependency edges pointing forward, predecessor
  * counts, group truncations as consecutive parts with edges on the first,
  * the ready list, products joined into TRSMs, and a model run of the
  * factorisation kernel's ready-queue protocol with `ctas` CTAs (> 8) and
- * op durations drawn from `seed`.  stats (up to 12 entries): factorisation
+ * op durations drawn from `seed`.  stats (up to 13 entries): factorisation
  * ops, edges, groups, initially ready ops; forward ops, joined products;
  * backward ops, joined products; matvec ops; model makespan; leaves; rank
- * slots.  Returns HLC_OK, HLC_ERR_STATE with the first violation in msg
- * (msglen bytes, NUL-terminated), HLC_ERR_ARG or HLC_ERR_OOM.
+ * slots; milliseconds of planning the factorisation.  Returns HLC_OK,
+ * HLC_ERR_STATE with the first violation in msg (msglen bytes,
+ * NUL-terminated), HLC_ERR_ARG or HLC_ERR_OOM.
  */
-int hlc_selftest_plans(int64_t n, int leaf, double eta, int kmax, int ctas, uint64_t seed, int64_t* stats,
-                       int nstats, char* msg, int msglen);
+int hlc_selftest_plans(int64_t n, int leaf, double eta, int geometry, int kmax, int ctas, uint64_t seed,
+                       int64_t* stats, int nstats, char* msg, int msglen);
 
 /* Dense expansion of C~ (symmetric) or L~ (lower) into an n x n column-major
  * host array in caller order; for small n only (n <= 16384). */

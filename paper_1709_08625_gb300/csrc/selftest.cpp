@@ -1,10 +1,12 @@
 // selftest.cpp -- host-only check of the planner's dataflow programs (no
-// device involved).  A synthetic cluster tree and block-cluster tree over
-// index intervals (midpoint bisection of [0, n), admissibility
-// min(size) <= eta * gap between the intervals) take the place of the
-// device-built trees; the factorisation, solve and matvec plans are built
-// from them exactly as for a real tree, and the checks are the invariants
-// the dependency-driven kernels rely on:
+// device involved).  A synthetic cluster tree and block-cluster tree take
+// the place of the device-built trees: midpoint bisection of the index
+// interval [0, n), with the clusters' boxes either the intervals themselves
+// (1-D) or the tight boxes of the points of a square grid numbered in Morton
+// order (2-D: the structure of uniformly spread points), and admissibility
+// min(diam) <= eta * dist between the boxes.  The factorisation, solve and
+// matvec plans are built from them exactly as for a real tree, and the
+// checks are the invariants the dependency-driven kernels rely on:
 //   * every plan passes validate_plan (views inside their buffers, rank
 //     slots inside the rank array);
 //   * every dependency edge points forward in flow order (the solve kernel
@@ -21,11 +23,14 @@
 //     protocol (G CTAs, seeded op durations, a group's parts waiting for
 //     each other) runs every op after all of its producers and finishes.
 
+#include <math.h>
 #include <stdint.h>
 #include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
+#include <cmath>
 #include <functional>
 #include <queue>
 #include <random>
@@ -43,7 +48,18 @@ constexpr int kParts = 8;  // parts of a group truncation (the kernel's cluster 
 
 // Clusters: midpoint bisection of index intervals, breadth-first like the
 // device build (children of a cluster are consecutive).
-void synth_clusters(HTree& T, int64_t n, int leaf) {
+// grid point of Morton index i: x from the even bits, y from the odd ones
+inline int64_t morton_compact(uint64_t v) {
+  uint64_t x = v & 0x5555555555555555ull;
+  x = (x | (x >> 1)) & 0x3333333333333333ull;
+  x = (x | (x >> 2)) & 0x0f0f0f0f0f0f0f0full;
+  x = (x | (x >> 4)) & 0x00ff00ff00ff00ffull;
+  x = (x | (x >> 8)) & 0x0000ffff0000ffffull;
+  x = (x | (x >> 16)) & 0x00000000ffffffffull;
+  return (int64_t)x;
+}
+
+void synth_clusters(HTree& T, int64_t n, int leaf, int geometry) {
   T.cl.clear();
   Cluster root{};
   root.lo = 0;
@@ -70,11 +86,37 @@ void synth_clusters(HTree& T, int64_t n, int leaf) {
   T.depth = 0;
   for (int64_t i = 0; i < (int64_t)T.cl.size(); ++i) {
     Cluster& C = T.cl[i];
-    C.bmin[0] = (double)C.lo / (double)n;
-    C.bmax[0] = (double)C.hi / (double)n;
-    C.bmin[1] = C.bmax[1] = 0.0;
+    if (geometry == 0) {
+      C.bmin[0] = (double)C.lo;
+      C.bmax[0] = (double)C.hi - 1.0;
+      C.bmin[1] = C.bmax[1] = 0.0;
+    } else {
+      C.bmin[0] = C.bmin[1] = 1e300;
+      C.bmax[0] = C.bmax[1] = -1e300;
+      for (int64_t p = C.lo; p < C.hi; ++p) {
+        const double x = (double)morton_compact((uint64_t)p), y = (double)morton_compact((uint64_t)p >> 1);
+        C.bmin[0] = std::min(C.bmin[0], x);
+        C.bmax[0] = std::max(C.bmax[0], x);
+        C.bmin[1] = std::min(C.bmin[1], y);
+        C.bmax[1] = std::max(C.bmax[1], y);
+      }
+    }
     T.depth = std::max(T.depth, C.level);
   }
+}
+
+double box_diam(const Cluster& c) {
+  const double a = c.bmax[0] - c.bmin[0], b = c.bmax[1] - c.bmin[1];
+  return std::sqrt(a * a + b * b);
+}
+
+double box_dist(const Cluster& r, const Cluster& s) {
+  double d2 = 0.0;
+  for (int k = 0; k < 2; ++k) {
+    const double g = std::max(0.0, std::max(r.bmin[k] - s.bmax[k], s.bmin[k] - r.bmax[k]));
+    d2 += g * g;
+  }
+  return std::sqrt(d2);
 }
 
 // Block-cluster tree on the lower triangle, breadth-first: a diagonal block
@@ -115,8 +157,8 @@ void synth_blocks(HTree& T, double eta) {
       continue;
     }
     T.blk[b].diag = 0;
-    const int64_t gap = R.lo >= S.hi ? R.lo - S.hi : S.lo - R.hi;
-    const bool adm = gap > 0 && (double)std::min(R.size(), S.size()) <= eta * (double)gap;
+    const double d = box_dist(R, S);
+    const bool adm = d > 0.0 && std::min(box_diam(R), box_diam(S)) <= eta * d;
     if (adm) {
       T.blk[b].type = BT_LR;
     } else if (lr || ls) {
@@ -243,7 +285,7 @@ double simulate_queue(const Plan& P, int ctas, uint64_t seed, Check& ck) {
   // events: (time, kind, cta, op); kind 0 = op finished
   using Ev = std::tuple<double, int, int, int64_t>;
   std::priority_queue<Ev, std::vector<Ev>, std::greater<Ev>> ev;
-  std::vector<int64_t> waiting_slot(ctas, -1);  // slot a CTA has claimed and waits on
+  std::vector<int32_t> waiter(F, -1);  // the CTA that claimed a slot not filled yet
   std::vector<std::vector<std::pair<int, int64_t>>> group_wait(group_arrived.size());
   double now = 0.0;
   std::function<void(int)> claim;
@@ -271,7 +313,7 @@ double simulate_queue(const Plan& P, int ctas, uint64_t seed, Check& ck) {
     if (s < filled) {
       start(c, slot[s]);
     } else {
-      waiting_slot[c] = s;
+      waiter[s] = c;
     }
   };
   auto push = [&](int32_t v) {
@@ -279,11 +321,7 @@ double simulate_queue(const Plan& P, int ctas, uint64_t seed, Check& ck) {
     for (int p = 0; p < np; ++p) {
       const int64_t s = filled++;
       slot[s] = v + p;
-      for (int c = 0; c < ctas; ++c)
-        if (waiting_slot[c] == s) {
-          waiting_slot[c] = -1;
-          start(c, slot[s]);
-        }
+      if (waiter[s] >= 0) start(waiter[s], slot[s]);
     }
   };
   for (int c = 0; c < ctas; ++c) claim(c);
@@ -316,26 +354,28 @@ double simulate_queue(const Plan& P, int ctas, uint64_t seed, Check& ck) {
 }  // namespace
 }  // namespace hlc
 
-extern "C" int hlc_selftest_plans(int64_t n, int leaf, double eta, int kmax, int ctas, uint64_t seed,
+extern "C" int hlc_selftest_plans(int64_t n, int leaf, double eta, int geometry, int kmax, int ctas, uint64_t seed,
                                   int64_t* stats, int nstats, char* msg, int msglen) {
   using namespace hlc;
-  if (n < 2 || leaf < 1 || leaf > 128 || !(eta > 0.0) || kmax < 1 || kmax > 128 || ctas <= kParts ||
-      (nstats > 0 && !stats) || (msglen > 0 && !msg))
+  if (n < 2 || n > ((int64_t)1 << 26) || leaf < 1 || leaf > 128 || !(eta > 0.0) || (geometry != 0 && geometry != 1) ||
+      kmax < 1 || kmax > 128 || ctas <= kParts || (nstats > 0 && !stats) || (msglen > 0 && !msg))
     return HLC_ERR_ARG;
   Check ck;
-  int64_t st[12] = {0};
+  int64_t st[13] = {0};
   try {
     HTree T;
     T.n = n;
     T.leaf = leaf;
     T.eta = eta;
     T.eps = 1e-6;
-    synth_clusters(T, n, leaf);
+    synth_clusters(T, n, leaf, geometry);
     synth_blocks(T, eta);
     collect_leaf_list(T);
     layout(T, kmax);
     Plan chol, fwd, bwd, mv;
+    const auto t0 = std::chrono::steady_clock::now();
     plan_cholesky(T, chol, false, true);
+    st[12] = (int64_t)std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     plan_solve(T, fwd, 0, 0, 1, false);
     plan_solve(T, bwd, 1, 0, 1, false);
     plan_matvec(T, mv, n, 2 * n, 1);
@@ -381,7 +421,7 @@ extern "C" int hlc_selftest_plans(int64_t n, int leaf, double eta, int kmax, int
   } catch (const std::bad_alloc&) {
     return HLC_ERR_OOM;
   }
-  for (int i = 0; i < nstats && i < 12; ++i) stats[i] = st[i];
+  for (int i = 0; i < nstats && i < 13; ++i) stats[i] = st[i];
   if (msglen > 0) {
     strncpy(msg, ck.err.c_str(), (size_t)msglen - 1);
     msg[msglen - 1] = '\0';
