@@ -300,10 +300,12 @@ int hlc_selftest_barrier_timeout(hlc_ctx* ctx);
  * counts, group truncations as consecutive parts with edges on the first,
  * the ready list, products joined into TRSMs, and a model run of the
  * factorisation kernel's ready-queue protocol with `ctas` CTAs (> 8) and
- * op durations drawn from `seed`.  stats (up to 13 entries): factorisation
+ * op durations drawn from `seed`.  stats (up to 15 entries): factorisation
  * ops, edges, groups, initially ready ops; forward ops, joined products;
  * backward ops, joined products; matvec ops; model makespan; leaves; rank
- * slots; milliseconds of planning the factorisation.  Returns HLC_OK,
+ * slots; milliseconds of planning the factorisation; a hash of the
+ * factorisation's op program and one of the solve and matvec programs (equal
+ * hashes: the same programs).  Returns HLC_OK,
  * HLC_ERR_STATE with the first violation in msg (msglen bytes,
  * NUL-terminated), HLC_ERR_ARG or HLC_ERR_OOM.
  */

@@ -184,6 +184,37 @@ struct Check {
 
 bool same_view(const Mv& a, const Mv& b) { return a.buf == b.buf && a.off == b.off && a.rs == b.rs; }
 
+// FNV-1a over the bytes of a plan's op program (op descriptors, terms,
+// launches and the dataflow arrays): equal hashes mean the same program
+template <class V>
+void hash_vec(uint64_t& h, const V& v) {
+  const unsigned char* p = reinterpret_cast<const unsigned char*>(v.data());
+  const size_t nb = v.size() * sizeof(typename V::value_type);
+  for (size_t i = 0; i < nb; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  h ^= (uint64_t)v.size();
+  h *= 1099511628211ull;
+}
+
+uint64_t plan_hash(const Plan& P) {
+  uint64_t h = 1469598103934665603ull;
+  hash_vec(h, P.gemm);
+  hash_vec(h, P.trsm);
+  hash_vec(h, P.potrf);
+  hash_vec(h, P.trunc);
+  hash_vec(h, P.terms);
+  hash_vec(h, P.launches);
+  hash_vec(h, P.flow);
+  hash_vec(h, P.npred);
+  hash_vec(h, P.succ_off);
+  hash_vec(h, P.succ);
+  hash_vec(h, P.ready0);
+  h ^= (uint64_t)P.tmp_doubles * 31 + (uint64_t)P.tmp_slots;
+  return h;
+}
+
 // The flow invariants of one plan; returns its number of edges.
 int64_t check_flow(const Plan& P, const char* name, bool solve, Check& ck, int64_t* joins) {
   const int64_t F = (int64_t)P.flow.size();
@@ -361,7 +392,7 @@ extern "C" int hlc_selftest_plans(int64_t n, int leaf, double eta, int geometry,
       kmax < 1 || kmax > 128 || ctas <= kParts || (nstats > 0 && !stats) || (msglen > 0 && !msg))
     return HLC_ERR_ARG;
   Check ck;
-  int64_t st[13] = {0};
+  int64_t st[15] = {0};
   try {
     HTree T;
     T.n = n;
@@ -402,6 +433,7 @@ extern "C" int hlc_selftest_plans(int64_t n, int leaf, double eta, int geometry,
         st[1] = edges;
         st[2] = P.ngroups;
         st[3] = (int64_t)P.ready0.size();
+        st[13] = (int64_t)plan_hash(P);
       } else if (k == 1) {
         st[4] = (int64_t)P.flow.size();
         st[5] = joins;
@@ -411,6 +443,7 @@ extern "C" int hlc_selftest_plans(int64_t n, int leaf, double eta, int geometry,
       } else {
         st[8] = (int64_t)P.flow.size();
       }
+      if (k > 0) st[14] = (int64_t)(((uint64_t)st[14] * 1099511628211ull) ^ plan_hash(P));
     }
     if (ck.err.empty()) {
       const double span = simulate_queue(chol, ctas, seed, ck);
@@ -421,7 +454,7 @@ extern "C" int hlc_selftest_plans(int64_t n, int leaf, double eta, int geometry,
   } catch (const std::bad_alloc&) {
     return HLC_ERR_OOM;
   }
-  for (int i = 0; i < nstats && i < 13; ++i) stats[i] = st[i];
+  for (int i = 0; i < nstats && i < 15; ++i) stats[i] = st[i];
   if (msglen > 0) {
     strncpy(msg, ck.err.c_str(), (size_t)msglen - 1);
     msg[msglen - 1] = '\0';

@@ -220,17 +220,18 @@ def fit_opts(step=None, size_tol=None, max_iter=None, free_mask=None):
 
 
 SELFTEST_PLAN_STATS = ("factor_ops", "factor_edges", "groups", "ready0", "fwd_ops", "fwd_joins", "bwd_ops",
-                       "bwd_joins", "mv_ops", "model_makespan", "leaves", "rank_slots", "plan_ms")
+                       "bwd_joins", "mv_ops", "model_makespan", "leaves", "rank_slots", "plan_ms", "factor_hash",
+                       "solve_hash")
 
 
 def selftest_plans(n, leaf=32, eta=2.0, kmax=64, ctas=16, seed=1, geometry=1):
     """hlc_selftest_plans (host only): the planner's dataflow invariants on a
     synthetic tree over [0, n) (geometry 1: a Morton-numbered grid, 0:
     intervals).  Returns (status, message, stats dict)."""
-    stats = np.zeros(13, dtype=np.int64)
+    stats = np.zeros(15, dtype=np.int64)
     msg = ctypes.create_string_buffer(512)
     st = hlc_selftest_plans(int(n), int(leaf), float(eta), int(geometry), int(kmax), int(ctas), int(seed),
-                            _ptr(stats), 13, msg, 512)
+                            _ptr(stats), 15, msg, 512)
     return st, msg.value.decode(), dict(zip(SELFTEST_PLAN_STATS, (int(v) for v in stats)))
 
 
