@@ -294,8 +294,9 @@ int hlc_selftest_barrier_timeout(hlc_ctx* ctx);
  * boxes: geometry 0 the intervals themselves, geometry 1 the tight boxes of
  * a square grid's points numbered in Morton order, n <= 2^26) and
  * block-cluster tree (admissible iff min(diam) <= eta * dist), the
- * H-Cholesky (a7), forward and backward solve (a9, a10) and matvec plans at
- * rank capacity kmax, and checks what the dependency-driven kernels rely on:
+ * H-Cholesky (a7, also with accumulated updates), forward and backward solve
+ * (a9, a10), matvec and factor-product (f2) plans at rank capacity kmax, and
+ * checks what the dependency-driven kernels rely on:
  * plans inside their buffers, dependency edges pointing forward, predecessor
  * counts, group truncations as consecutive parts with edges on the first,
  * the ready list, products joined into TRSMs, and a model run of the

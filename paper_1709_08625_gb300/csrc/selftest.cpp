@@ -4,9 +4,10 @@
 // interval [0, n), with the clusters' boxes either the intervals themselves
 // (1-D) or the tight boxes of the points of a square grid numbered in Morton
 // order (2-D: the structure of uniformly spread points), and admissibility
-// min(diam) <= eta * dist between the boxes.  The factorisation, solve and
-// matvec plans are built from them exactly as for a real tree, and the
-// checks are the invariants the dependency-driven kernels rely on:
+// min(diam) <= eta * dist between the boxes.  The factorisation (also with
+// accumulated updates), solve, matvec and factor-product plans are built
+// from them exactly as for a real tree, and the checks are the invariants
+// the dependency-driven kernels rely on:
 //   * every plan passes validate_plan (views inside their buffers, rank
 //     slots inside the rank array);
 //   * every dependency edge points forward in flow order (the solve kernel
@@ -410,14 +411,21 @@ extern "C" int hlc_selftest_plans(int64_t n, int leaf, double eta, int geometry,
     plan_solve(T, fwd, 0, 0, 1, false);
     plan_solve(T, bwd, 1, 0, 1, false);
     plan_matvec(T, mv, n, 2 * n, 1);
+    // also checked, not counted in the stats: the factorisation with
+    // accumulated updates and the products with the factor and its transpose
+    Plan chol_acc, lmv, lmvt;
+    plan_cholesky(T, chol_acc, true, true);
+    plan_trmv(T, lmv, 0, 0, 1, false);
+    plan_trmv(T, lmvt, 1, 0, 1, false);
     const struct {
       const Plan* P;
       const char* name;
       bool solve;
-      int32_t arena;  // the buffer the plan's matrix lives in
-    } plans[4] = {{&chol, "factorisation", false, BUF_L}, {&fwd, "forward solve", true, BUF_L},
-                  {&bwd, "backward solve", true, BUF_L}, {&mv, "matvec", true, BUF_C}};
-    for (int k = 0; k < 4 && ck.err.empty(); ++k) {
+    } plans[7] = {{&chol, "factorisation", false},        {&fwd, "forward solve", true},
+                  {&bwd, "backward solve", true},         {&mv, "matvec", true},
+                  {&chol_acc, "accumulated factorisation", false}, {&lmv, "product with L", true},
+                  {&lmvt, "product with L^T", true}};
+    for (int k = 0; k < 7 && ck.err.empty(); ++k) {
       const Plan& P = *plans[k].P;
       int64_t bufsize[NBUF] = {0, 0, 0, 0};
       bufsize[BUF_L] = T.arena_doubles;
@@ -440,11 +448,12 @@ extern "C" int hlc_selftest_plans(int64_t n, int leaf, double eta, int geometry,
       } else if (k == 2) {
         st[6] = (int64_t)P.flow.size();
         st[7] = joins;
-      } else {
+      } else if (k == 3) {
         st[8] = (int64_t)P.flow.size();
       }
-      if (k > 0) st[14] = (int64_t)(((uint64_t)st[14] * 1099511628211ull) ^ plan_hash(P));
+      if (k > 0 && k < 4) st[14] = (int64_t)(((uint64_t)st[14] * 1099511628211ull) ^ plan_hash(P));
     }
+    if (ck.err.empty()) simulate_queue(chol_acc, ctas, seed + 1, ck);
     if (ck.err.empty()) {
       const double span = simulate_queue(chol, ctas, seed, ck);
       st[9] = (int64_t)span;
